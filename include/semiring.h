@@ -1,0 +1,155 @@
+/*
+ * semiring.h — C ABI of the GB300 semiring library (libsemiring.so).
+ *
+ * Matrices over the Boolean semiring and over the saturating anti-distance
+ * semiring of de Bondt, "Fast algorithms for anti-distance matrices as a
+ * generalization of Boolean matrices" (arXiv 1705.08743):
+ *
+ *   Boolean (Section 2):          entries {0,1},  a ⊕ b = max(a,b),  a ⊗ b = min(a,b)
+ *   anti-distance (Sections 3-4): entries {0..S}, a ⊕ b = max(a,b),  a ⊗ b = max(a+b−S, 0)
+ *                                 S = 255 (u8) or 65535 (u16); entry S − d stands
+ *                                 for distance d, 0 for "no path / distance >= S".
+ *
+ * Conventions shared by every call
+ *  - Pointers to matrix data are DEVICE pointers owned by the caller; the
+ *    library never frees them.  Matrices are row-major with a leading
+ *    dimension ld >= row width, in elements (u8/u16) or in words of the
+ *    Boolean word type (32- or 64-bit).
+ *  - Boolean matrices are bit-packed: entry (i, j) is bit (j mod w) of word
+ *    floor(j / w) of row i (w = 32 or 64), i.e. bit (j & 7) of byte (j >> 3)
+ *    on a little-endian machine (Section 4, matBool).  Bits past the logical
+ *    width are "pad bits": they are ignored on input and written 0 on output.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Calls only
+ *    enqueue work and return; results are ordered on `stream`.  A call that
+ *    returns SR_OK has launched all its kernels; device-side errors surface at
+ *    the next synchronisation (sr_stream_status reports bounded-wait timeouts).
+ *  - Vector (16-byte) loads are used when every base pointer is 16-byte
+ *    aligned and ld·(bytes per element) is a multiple of 16; any other
+ *    alignment is accepted and runs a slower element-wise path.
+ *  - Errors: every call returns an sr_status; on failure nothing was enqueued
+ *    and sr_last_error() (per calling thread) says why.  No C++ exception
+ *    crosses this interface.
+ *  - `ctx` may be NULL for calls that need no workspace (products, closures
+ *    by the blocked Warshall method, encoding).  Calls that share one ctx and
+ *    use its workspace must be ordered on one stream.
+ */
+#ifndef SEMIRING_H
+#define SEMIRING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SR_OK = 0,
+    SR_EINVAL = 1,     /* bad argument: size, ld, dtype, overlap, NULL pointer */
+    SR_ENOMEM = 2,     /* workspace or serving memory budget too small */
+    SR_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    SR_ETIMEOUT = 4,   /* a bounded device-side or host-side wait gave up */
+    SR_EAGAIN = 5,     /* serving: no free slot or memory now; retry later */
+    SR_EBUSY = 6,      /* serving: ticket not finished yet */
+    SR_ENOTFOUND = 7   /* serving: unknown or already released ticket */
+} sr_status;
+
+typedef enum {
+    SR_BOOL_W32 = 0,   /* Boolean, 32 columns per uint32 word */
+    SR_BOOL_W64 = 1,   /* Boolean, 64 columns per uint64 word */
+    SR_U8 = 2,         /* anti-distance, S = 255, one uint8 per entry */
+    SR_U16 = 3         /* anti-distance, S = 65535, one uint16 per entry */
+} sr_dtype;
+
+typedef enum {
+    SR_CLOSURE_WARSHALL = 0,   /* three-phase blocked Warshall/Floyd (Section 2) */
+    SR_CLOSURE_SQUARING = 1    /* A ⊗ (I ⊕ A)^(2^m), m = ceil(log2(D−1)) (Section 2) */
+} sr_closure_method;
+
+typedef enum {
+    SR_OP_ANTIDIST_MUL = 0,
+    SR_OP_BOOL_MUL = 1,
+    SR_OP_ANTIDIST_CLOSURE = 2,
+    SR_OP_BOOL_CLOSURE = 3
+} sr_op;
+
+typedef struct sr_ctx sr_ctx;
+
+typedef struct {
+    size_t workspace_bytes;    /* device workspace allocated by sr_create (0: none) */
+    int spin_limit;            /* iterations before a device-side wait gives up (0: default) */
+    int reserved[6];
+} sr_config;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device; cfg may be NULL (defaults).
+ * Allocates cfg->workspace_bytes of device memory once; no later call of the
+ * library allocates device memory on this context's behalf except the serving
+ * loop (sr_serve_*), which allocates its arena when it starts. */
+sr_status sr_create(sr_ctx **out, const sr_config *cfg);
+void sr_destroy(sr_ctx *ctx);
+/* Message of the last failed call made by this thread ("" if none). */
+const char *sr_last_error(void);
+/* Library version string. */
+const char *sr_version(void);
+/* Device workspace bytes a call would need (0 for calls that need none). */
+sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size_t *bytes);
+
+/* ---------------------------------------------------------------- encoding (Sections 3-4) */
+
+/* T (R×C, dtype SR_U8 or SR_U16) := anti-distance encoding of integer edge
+ * lengths W (same element type, same shape): entry = S − w for 0 < w < S,
+ * and 0 for w = 0 ("no edge") or w >= S (not distinguished from infinity,
+ * Section 3).  W and T may be the same buffer. */
+sr_status antidist_encode(sr_ctx *ctx, const void *W, int64_t ldw, void *T, int64_t ldt,
+                          int64_t R, int64_t C, sr_dtype dtype, void *stream);
+
+/* M (R×C bits, dtype SR_BOOL_W32/W64) := dense 0/1 bytes (nonzero = 1), pad bits 0. */
+sr_status bool_pack(sr_ctx *ctx, const uint8_t *dense, int64_t ldd, void *M, int64_t ldm,
+                    int64_t R, int64_t C, sr_dtype dtype, void *stream);
+/* dense (R×C bytes) := 0/1 entries of the bit matrix M. */
+sr_status bool_unpack(sr_ctx *ctx, const void *M, int64_t ldm, uint8_t *dense, int64_t ldd,
+                      int64_t R, int64_t C, sr_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------- products (Section 2 formula; Section 4 listings) */
+
+/* C := (accumulate ? C : 0) ⊕ A ⊗ B with A R×K, B K×N, C R×N, anti-distance
+ * (dtype SR_U8 or SR_U16).  (A ⊗ B)_ij = max over k of max(A_ik + B_kj − S, 0).
+ * C must not overlap A or B (the aliased form is the closure).
+ * R, K, N >= 1 and < 2^31. */
+sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb,
+                       void *C, int64_t ldc, int64_t R, int64_t K, int64_t N,
+                       sr_dtype dtype, int accumulate, void *stream);
+
+/* Boolean product of bit matrices: C := (accumulate ? C : 0) ⊕ A ⊗ B,
+ * (A ⊗ B)_ij = OR over k of (A_ik AND B_kj).  dtype SR_BOOL_W32 or W64;
+ * lda/ldb/ldc in words.  C must not overlap A or B. */
+sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb,
+                   void *C, int64_t ldc, int64_t R, int64_t K, int64_t N,
+                   sr_dtype dtype, int accumulate, void *stream);
+
+/* ---------------------------------------------------------------- closures (Section 2 Warshall; Section 3 Floyd) */
+
+/* In place: T (D×D) := A ⊕ A⊗A ⊕ A⊗A⊗A ⊕ ... (non-reflexive closure; T_ii is
+ * the best cycle through i).  Anti-distance dtype SR_U8 / SR_U16; three-phase
+ * blocked Warshall/Floyd.  Needs no workspace. */
+sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
+                           void *stream);
+
+/* In place Boolean transitive closure of the D×D bit matrix T (dtype
+ * SR_BOOL_W32/W64).  method SR_CLOSURE_WARSHALL needs no workspace;
+ * SR_CLOSURE_SQUARING needs sr_workspace_query() bytes of ctx workspace. */
+sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
+                       int method, void *stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Reads and clears the context's device status word (bounded waits that gave
+ * up), synchronising `stream` first.  SR_OK or SR_ETIMEOUT. */
+sr_status sr_stream_status(sr_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEMIRING_H */

@@ -1,0 +1,157 @@
+"""ctypes binding of libsemiring.so (include/semiring.h), argument marshalling only.
+
+Every function has the C name and argument order.  Pointer arguments accept
+an int (a device address) or any object with ``data_ptr()`` (a torch tensor);
+``stream`` accepts None (torch's current stream), an int handle, or an object
+with ``cuda_stream``.  A non-OK status raises SemiringError carrying the
+library's message.  No computation happens here: a missing library raises at
+import, and there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsemiring.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"` "
+        "(paper_1705_08743_gb300.build.build()); there is no fallback implementation")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+# status codes / enums (include/semiring.h)
+SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ETIMEOUT, SR_EAGAIN, SR_EBUSY, SR_ENOTFOUND = range(8)
+SR_BOOL_W32, SR_BOOL_W64, SR_U8, SR_U16 = range(4)
+SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
+SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
+
+STATUS_NAMES = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ETIMEOUT",
+                5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND"}
+
+
+class SemiringError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sr_config(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_size_t), ("spin_limit", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+_vp, _i64, _int, _st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int
+
+_SIGS = {
+    "sr_create": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(sr_config)]),
+    "sr_destroy": (None, [_vp]),
+    "sr_last_error": (ctypes.c_char_p, []),
+    "sr_version": (ctypes.c_char_p, []),
+    "sr_workspace_query": (_st, [_int, _int, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "sr_stream_status": (_st, [_vp, _vp]),
+    "antidist_encode": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
+    "bool_pack": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
+    "bool_unpack": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
+    "antidist_mul": (_st, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp]),
+    "bool_mul": (_st, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp]),
+    "antidist_closure": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
+    "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "value"):
+        return x.value
+    raise TypeError(f"cannot take a device pointer from {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st: int, fn: str):
+    if st != SR_OK:
+        raise SemiringError(st, fn, last_error())
+
+
+def last_error() -> str:
+    return (lib.sr_last_error() or b"").decode()
+
+
+def version() -> str:
+    return lib.sr_version().decode()
+
+
+def sr_create(workspace_bytes: int = 0, spin_limit: int = 0):
+    cfg = sr_config(workspace_bytes=workspace_bytes, spin_limit=spin_limit)
+    h = _vp()
+    _check(lib.sr_create(ctypes.byref(h), ctypes.byref(cfg)), "sr_create")
+    return h.value
+
+
+def sr_destroy(ctx):
+    lib.sr_destroy(ctx)
+
+
+def sr_workspace_query(op: int, dtype: int, D: int, method: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.sr_workspace_query(op, dtype, D, method, ctypes.byref(n)), "sr_workspace_query")
+    return n.value
+
+
+def sr_stream_status(ctx, stream=None):
+    _check(lib.sr_stream_status(ctx, _stream(stream)), "sr_stream_status")
+
+
+def antidist_encode(ctx, W, ldw, T, ldt, R, C, dtype, stream=None):
+    _check(lib.antidist_encode(ctx, _ptr(W), ldw, _ptr(T), ldt, R, C, dtype, _stream(stream)), "antidist_encode")
+
+
+def bool_pack(ctx, dense, ldd, M, ldm, R, C, dtype, stream=None):
+    _check(lib.bool_pack(ctx, _ptr(dense), ldd, _ptr(M), ldm, R, C, dtype, _stream(stream)), "bool_pack")
+
+
+def bool_unpack(ctx, M, ldm, dense, ldd, R, C, dtype, stream=None):
+    _check(lib.bool_unpack(ctx, _ptr(M), ldm, _ptr(dense), ldd, R, C, dtype, _stream(stream)), "bool_unpack")
+
+
+def antidist_mul(ctx, A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate=0, stream=None):
+    _check(lib.antidist_mul(ctx, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, R, K, N, dtype, int(accumulate),
+                            _stream(stream)), "antidist_mul")
+
+
+def bool_mul(ctx, A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate=0, stream=None):
+    _check(lib.bool_mul(ctx, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, R, K, N, dtype, int(accumulate),
+                        _stream(stream)), "bool_mul")
+
+
+def antidist_closure(ctx, T, ldt, D, dtype, stream=None):
+    _check(lib.antidist_closure(ctx, _ptr(T), ldt, D, dtype, _stream(stream)), "antidist_closure")
+
+
+def bool_closure(ctx, T, ldt, D, dtype, method=SR_CLOSURE_WARSHALL, stream=None):
+    _check(lib.bool_closure(ctx, _ptr(T), ldt, D, dtype, method, _stream(stream)), "bool_closure")

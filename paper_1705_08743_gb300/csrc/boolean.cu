@@ -1,0 +1,438 @@
+// Boolean semiring product and closure on bit-packed rows (Section 2; Section 4 matBool).
+//
+// Entry (i, j) is bit (j mod 32) of 32-bit word floor(j / 32) of row i (a
+// 64-bit-word matrix is the same bits, two 32-bit words per 64-bit word).
+//
+// Product C := (accumulate ? C : 0) ⊕ A ⊗ B: for every k with A_ik = 1, row k
+// of B is ORed into row i of C, 32 columns per word operation (the matBool
+// listing does the same with 64-bit blocks).  Each CTA owns a BM×BNW-word tile
+// of C in registers; k-panels of A (words) and B (rows of words) arrive in
+// shared memory by cp.async; per k a thread expands bit k of each of its TM
+// rows of A to an all-ones/all-zeros mask and ORs (B word AND mask) into its
+// TNW accumulator words.
+//
+// Closure: the same three-phase blocked Warshall as the anti-distance closure
+// (antidist.cu), with PB-bit blocks.
+
+#include <algorithm>
+
+#include "sr_common.cuh"
+#include "sr_kernels.h"
+
+namespace sr {
+
+__device__ __forceinline__ int bremap(int x, int skip0, int skipw) { return x < skip0 ? x : x + skipw; }
+
+// valid-bit mask of physical word w of a row with nbits logical bits
+__device__ __forceinline__ uint32_t word_mask(int w, int nbits)
+{
+    const int lo = w * 32;
+    if (lo + 32 <= nbits) return 0xFFFFFFFFu;
+    if (lo >= nbits) return 0u;
+    return (1u << (nbits - lo)) - 1u;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_ptr, const void *gptr, bool valid)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem_ptr);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gptr), "r"(n));
+}
+__device__ __forceinline__ void cp_async4(void *smem_ptr, const void *gptr, bool valid)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem_ptr);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gptr), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// -------------------------------------------------------------------------
+// Product kernel (also phase 3 of the closure)
+// -------------------------------------------------------------------------
+template <int BM, int BNW, int BKW, int TM, int TNW>
+struct BoolCfg {
+    static constexpr int TR = BM / TM, TC = BNW / TNW, THREADS = TR * TC;
+    static constexpr int BKB = BKW * 32;
+    static constexpr size_t SMEM = (size_t)2 * (BKW * BM + BKB * BNW) * sizeof(uint32_t);
+    static_assert(TM % 4 == 0 && TNW % 4 == 0, "vector groups");
+    static_assert(THREADS % 32 == 0, "warps");
+};
+
+template <int BM, int BNW, int BKW, int TM, int TNW, bool VEC>
+__global__ void __launch_bounds__(BoolCfg<BM, BNW, BKW, TM, TNW>::THREADS)
+bool_mul_kernel(BoolArgs p)
+{
+    using Cfg = BoolCfg<BM, BNW, BKW, TM, TNW>;
+    constexpr int TR = Cfg::TR, TC = Cfg::TC, THREADS = Cfg::THREADS, BKB = Cfg::BKB;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sA = smem;                         // [2][BKW][BM]  (word kw of each row; transposed)
+    uint32_t *sB = smem + 2 * BKW * BM;          // [2][BKB][BNW]
+
+    const int tid = threadIdx.x;
+    const int tc = tid % TC, tr = tid / TC;
+    const int row0 = blockIdx.y * BM, w0 = blockIdx.x * BNW;
+    const int kwords = (p.K + 31) / 32;          // words of A rows holding bits < K
+
+    uint32_t acc[TM][TNW];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+#pragma unroll
+        for (int u = 0; u < TNW; ++u) {
+            const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
+            uint32_t v = 0u;
+            if (p.accumulate && r < p.R && w < p.ncw)
+                v = p.C[(int64_t)bremap(r, p.skip0, p.skipw) * p.ldc + bremap(w, p.skip0w, p.skipww)];
+            acc[i][u] = v;
+        }
+    }
+
+    // A tile: BM rows × BKW words, stored transposed; B tile: BKB rows × BNW words
+    auto stage = [&](int kt, int buf) {
+        const int kw0 = kt * BKW;
+        // A: one thread per (row, word); bits >= K are masked when read
+        for (int t = tid; t < BM * BKW; t += THREADS) {
+            const int i = t % BM, e = t / BM;
+            const int r = row0 + i, kw = kw0 + e;
+            const bool ok = r < p.R && kw < kwords;
+            const uint32_t *src = p.A + (ok ? (int64_t)bremap(r, p.skip0, p.skipw) * p.lda + kw : 0);
+            uint32_t *dst = sA + (buf * BKW + e) * BM + i;
+            if (VEC)
+                cp_async4(dst, src, ok);
+            else
+                *dst = ok ? *src : 0u;
+        }
+        // B: rows k of B, groups of 4 words
+        for (int t = tid; t < BKB * (BNW / 4); t += THREADS) {
+            const int g = t % (BNW / 4), kr = t / (BNW / 4);
+            const int k = kt * BKB + kr;
+            const int w = w0 + g * 4;
+            uint32_t *dst = sB + (buf * BKB + kr) * BNW + g * 4;
+            const bool rowok = k < p.K;
+            if (VEC) {
+                // the 4-word group never straddles the excluded range (multiples of 4 words)
+                const uint32_t *src = p.B + (int64_t)(rowok ? k : 0) * p.ldb + bremap(w < p.ncw ? w : 0, p.skip0w, p.skipww);
+                cp_async16(dst, src, rowok && w < p.ncw);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t v = 0u;
+                    if (rowok && w + e < p.ncw)
+                        v = p.B[(int64_t)k * p.ldb + bremap(w + e, p.skip0w, p.skipww)];
+                    dst[e] = v;
+                }
+            }
+        }
+        if (VEC) cp_async_commit();
+    };
+
+    const int nkt = (p.K + BKB - 1) / BKB;
+    stage(0, 0);
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int buf = kt & 1;
+        if (VEC) cp_async_wait<0>();
+        __syncthreads();
+        if (kt + 1 < nkt)
+            stage(kt + 1, buf ^ 1);
+        const uint32_t *ap = sA + buf * BKW * BM + tr * 4;
+        const uint32_t *bp = sB + buf * BKB * BNW + tc * 4;
+#pragma unroll 1
+        for (int kw = 0; kw < BKW; ++kw) {
+            uint32_t a[TM];
+#pragma unroll
+            for (int g = 0; g < TM / 4; ++g) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(ap + kw * BM + g * 4 * TR);
+                a[4 * g] = v.x; a[4 * g + 1] = v.y; a[4 * g + 2] = v.z; a[4 * g + 3] = v.w;
+            }
+            const uint32_t km = word_mask(kt * BKW + kw, p.K);
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+                a[i] &= km;
+#pragma unroll 8
+            for (int bit = 0; bit < 32; ++bit) {
+                uint32_t b[TNW];
+                const uint32_t *brow = bp + (kw * 32 + bit) * BNW;
+#pragma unroll
+                for (int g = 0; g < TNW / 4; ++g) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(brow + g * 4 * TC);
+                    b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
+                }
+#pragma unroll
+                for (int i = 0; i < TM; ++i) {
+                    const uint32_t m = (uint32_t)((int32_t)(a[i] << (31 - bit)) >> 31);
+#pragma unroll
+                    for (int u = 0; u < TNW; ++u)
+                        acc[i][u] |= b[u] & m;
+                }
+            }
+        }
+        // the next iteration's barrier orders these reads before the next overwrite
+        // of this buffer (which is issued only after that barrier)
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+        if (r >= p.R)
+            continue;
+        uint32_t *dst = p.C + (int64_t)bremap(r, p.skip0, p.skipw) * p.ldc;
+#pragma unroll
+        for (int u = 0; u < TNW; ++u) {
+            const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
+            if (w < p.ncw) {
+                const int pw = bremap(w, p.skip0w, p.skipww);
+                dst[pw] = acc[i][u] & word_mask(pw, p.N);
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// Fused phases 1 + 2 of the Boolean blocked closure: PB rows per block, one
+// thread per row holding its PB/32 words.
+// -------------------------------------------------------------------------
+template <int PB>
+__global__ void __launch_bounds__(PB) bool_panel_kernel(uint32_t *T, int64_t ldt, int D, int rw, int kb)
+{
+    constexpr int PW = PB / 32;
+    __shared__ __align__(16) uint32_t sB[PB][PW];
+    __shared__ __align__(16) uint32_t rowbuf[2][PW];
+    const int i = threadIdx.x;
+    const int nb = (D + PB - 1) / PB;
+    const int k0 = kb * PB, bw = min(PB, D - k0);
+    const int kw0 = k0 / 32;
+
+    int role = 0, bi = kb, bj = kb;
+    if (blockIdx.x >= 1 && blockIdx.x < (unsigned)nb) {
+        role = 1; bj = (int)blockIdx.x - 1; if (bj >= kb) ++bj;
+    } else if (blockIdx.x >= (unsigned)nb) {
+        role = 2; bi = (int)blockIdx.x - nb; if (bi >= kb) ++bi;
+    }
+
+    // block words: rows [r0, r0+h), words [c0w, c0w + nw) with valid bits up to D
+    auto load_row = [&](int r0, int h, int c0w, uint32_t (&R)[PW]) {
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            uint32_t v = 0u;
+            if (i < h && c0w + u < rw)
+                v = T[(int64_t)(r0 + i) * ldt + c0w + u] & word_mask(c0w + u, D);
+            R[u] = v;
+        }
+    };
+    auto store_row = [&](int r0, int h, int c0w, const uint32_t (&R)[PW]) {
+        if (i >= h) return;
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if (c0w + u < rw)
+                T[(int64_t)(r0 + i) * ldt + c0w + u] = R[u] & word_mask(c0w + u, D);
+    };
+
+    // phase 1: Warshall on the diagonal block; pivot kk = 32 w + b
+    uint32_t X[PW];
+    load_row(k0, bw, kw0, X);
+#pragma unroll
+    for (int w = 0; w < PW; ++w) {
+        for (int b = 0; b < 32; ++b) {
+            const int kk = 32 * w + b;
+            if (kk >= bw)
+                break;
+            const int par = kk & 1;
+            if (i == kk) {
+#pragma unroll
+                for (int u = 0; u < PW; ++u) rowbuf[par][u] = X[u];
+            }
+            __syncthreads();
+            const uint32_t m = (uint32_t)((int32_t)(X[w] << (31 - b)) >> 31);
+#pragma unroll
+            for (int u = 0; u < PW; ++u) X[u] |= rowbuf[par][u] & m;
+        }
+    }
+    if (role == 0) {
+        store_row(k0, bw, kw0, X);
+        return;
+    }
+
+    // phase 2
+    const int r0 = bi * PB, h = min(PB, D - r0);
+    const int c0w = bj * PW;
+    uint32_t Y[PW], Arow[PW];
+    load_row(r0, h, c0w, Y);
+    if (role == 1) {            // Y := Y ⊕ T_kk ⊗ Y : A row = X (closed pivot block), B = old Y
+#pragma unroll
+        for (int u = 0; u < PW; ++u) { sB[i][u] = Y[u]; Arow[u] = X[u]; }
+    } else {                    // Y := Y ⊕ Y ⊗ T_kk : A row = old Y, B = X
+#pragma unroll
+        for (int u = 0; u < PW; ++u) { sB[i][u] = X[u]; Arow[u] = Y[u]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < PW; ++w) {
+        for (int b = 0; b < 32; ++b) {
+            const int kk = 32 * w + b;
+            if (kk >= bw) break;
+            const uint32_t m = (uint32_t)((int32_t)(Arow[w] << (31 - b)) >> 31);
+#pragma unroll
+            for (int u = 0; u < PW; ++u) Y[u] |= sB[kk][u] & m;
+        }
+    }
+    store_row(r0, h, c0w, Y);
+}
+
+// -------------------------------------------------------------------------
+// Encoding helpers
+// -------------------------------------------------------------------------
+// one warp per (row, word): lane l reads column 32 w + l, ballot packs the word
+__global__ void bool_pack_kernel(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C, int rw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t total = (int64_t)R * rw;
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; t < total; t += nwarps) {
+        const int r = (int)(t / rw), w = (int)(t % rw);
+        const int c = 32 * w + lane;
+        const bool bit = c < C && dense[(int64_t)r * ldd + c] != 0;
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0)
+            M[(int64_t)r * ldm + w] = word;
+    }
+}
+
+__global__ void bool_unpack_kernel(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C)
+{
+    const int64_t total = (int64_t)R * C;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / C), c = (int)(t % C);
+        dense[(int64_t)r * ldd + c] = (uint8_t)((M[(int64_t)r * ldm + c / 32] >> (c % 32)) & 1u);
+    }
+}
+
+__global__ void bool_identity_or_kernel(uint32_t *M, int64_t ldm, int D)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D; i += gridDim.x * blockDim.x)
+        M[(int64_t)i * ldm + i / 32] |= 1u << (i % 32);
+}
+
+__global__ void copy_rows_kernel(const uint32_t *src, int64_t lds, uint32_t *dst, int64_t ldd, int R, int rw)
+{
+    const int64_t total = (int64_t)R * rw;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / rw), w = (int)(t % rw);
+        dst[(int64_t)r * ldd + w] = src[(int64_t)r * lds + w];
+    }
+}
+
+// zero the pad bits of every row (bits >= D) so the closure's invariant holds
+__global__ void bool_clear_pad_kernel(uint32_t *M, int64_t ldm, int R, int D, int rw)
+{
+    const int w0 = D / 32;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+        for (int w = w0; w < rw; ++w)
+            M[(int64_t)r * ldm + w] &= word_mask(w, D);
+}
+
+// -------------------------------------------------------------------------
+// Host launchers
+// -------------------------------------------------------------------------
+template <int BM, int BNW, int BKW, int TM, int TNW>
+static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
+{
+    using Cfg = BoolCfg<BM, BNW, BKW, TM, TNW>;
+    dim3 grid((a.ncw + BNW - 1) / BNW, (a.R + BM - 1) / BM);
+    if (grid.y > 65535u)
+        return fail(SR_EINVAL, "bool_mul: R too large for the tile grid (%d)", a.R);
+    auto kern = vec ? bool_mul_kernel<BM, BNW, BKW, TM, TNW, true> : bool_mul_kernel<BM, BNW, BKW, TM, TNW, false>;
+    static bool attr[2][kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[vec][dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        attr[vec][dev] = true;
+    }
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+    SR_CUDA_CHECK(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s)
+{
+    if (a.R <= 0 || a.ncw <= 0)
+        return SR_OK;
+    return launch_bool_cfg<128, 64, 4, 4, 16>(a, vec, s);
+}
+
+sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
+{
+    constexpr int PB = 128, PW = PB / 32;
+    const int nb = (D + PB - 1) / PB;
+    bool_clear_pad_kernel<<<(D + 255) / 256, 256, 0, s>>>(T, ldt, D, D, rw);
+    SR_CUDA_CHECK(cudaGetLastError());
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * PB, bw = std::min(PB, D - k0);
+        bool_panel_kernel<PB><<<2 * nb - 1, PB, 0, s>>>(T, ldt, D, rw, kb);
+        SR_CUDA_CHECK(cudaGetLastError());
+        if (nb > 1) {
+            BoolArgs a;
+            a.A = T + k0 / 32;
+            a.B = T + (int64_t)k0 * ldt;
+            a.C = T;
+            a.lda = a.ldb = a.ldc = ldt;
+            a.R = D - bw;
+            a.K = bw;
+            a.N = D;
+            a.accumulate = 1;
+            a.skip0 = k0;
+            a.skipw = bw;
+            if (kb + 1 < nb) {
+                a.ncw = rw - PW;
+                a.skip0w = k0 / 32;
+                a.skipww = PW;
+            } else {
+                a.ncw = k0 / 32;
+                a.skip0w = a.ncw;
+                a.skipww = 0;
+            }
+            SR_TRY(launch_bool_mul(a, vec, s));
+        }
+    }
+    return SR_OK;
+}
+
+sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C, int rw,
+                           int num_sms, cudaStream_t s)
+{
+    const int64_t words = (int64_t)R * rw;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 7) / 8, (int64_t)num_sms * 16));
+    bool_pack_kernel<<<blocks, 256, 0, s>>>(dense, ldd, M, ldm, R, C, rw);
+    SR_CUDA_CHECK(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C,
+                             int num_sms, cudaStream_t s)
+{
+    const int64_t n = (int64_t)R * C;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
+    bool_unpack_kernel<<<blocks, 256, 0, s>>>(M, ldm, dense, ldd, R, C);
+    SR_CUDA_CHECK(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status launch_bool_identity_or(uint32_t *M, int64_t ldm, int D, cudaStream_t s)
+{
+    bool_identity_or_kernel<<<(D + 255) / 256, 256, 0, s>>>(M, ldm, D);
+    SR_CUDA_CHECK(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status launch_copy_rows(const uint32_t *src, int64_t lds, uint32_t *dst, int64_t ldd, int R, int rw,
+                           cudaStream_t s)
+{
+    const int64_t n = (int64_t)R * rw;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+    copy_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, dst, ldd, R, rw);
+    SR_CUDA_CHECK(cudaGetLastError());
+    return SR_OK;
+}
+
+}  // namespace sr

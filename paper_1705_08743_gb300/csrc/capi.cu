@@ -1,0 +1,374 @@
+// C ABI of the semiring library: argument checks, context, dispatch to kernels.
+// Every exported function returns an sr_status and never throws.
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "sr_common.cuh"
+#include "sr_kernels.h"
+#include "sr_ctx.h"
+
+namespace sr {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+sr_status fail(sr_status st, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+sr_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return SR_ECUDA;
+}
+
+int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) d = 0;
+    return d < 0 ? 0 : (d >= kMaxDevices ? kMaxDevices - 1 : d);
+}
+
+int device_sm_count()
+{
+    static int cache[kMaxDevices] = {};
+    const int d = current_device();
+    if (cache[d] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 1;
+        cache[d] = n;
+    }
+    return cache[d];
+}
+
+// ------------------------------------------------------------------ checks
+static bool is_anti(sr_dtype t) { return t == SR_U8 || t == SR_U16; }
+static bool is_bool(sr_dtype t) { return t == SR_BOOL_W32 || t == SR_BOOL_W64; }
+static int esize(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : t == SR_BOOL_W32 ? 4 : 8; }
+// row width in the dtype's own units (entries or words) for a row of n entries
+static int64_t row_units(sr_dtype t, int64_t n)
+{
+    if (t == SR_BOOL_W32) return (n + 31) / 32;
+    if (t == SR_BOOL_W64) return (n + 63) / 64;
+    return n;
+}
+static int u32_per_unit(sr_dtype t) { return t == SR_BOOL_W64 ? 2 : 1; }
+
+static sr_status check_dim(const char *fn, const char *name, int64_t v)
+{
+    if (v <= 0 || v > 0x7fffffffLL)
+        return fail(SR_EINVAL, "%s: %s = %lld must be in [1, 2^31)", fn, name, (long long)v);
+    return SR_OK;
+}
+
+static sr_status check_mat(const char *fn, const char *name, const void *p, int64_t ld, int64_t rows,
+                           int64_t cols, sr_dtype t)
+{
+    if (!p)
+        return fail(SR_EINVAL, "%s: %s is NULL", fn, name);
+    const int64_t w = row_units(t, cols);
+    if (ld < w)
+        return fail(SR_EINVAL, "%s: ld of %s (%lld) is below its row width (%lld)", fn, name, (long long)ld,
+                    (long long)w);
+    if (ld > (int64_t)1 << 40 || rows * ld > ((int64_t)1 << 46))
+        return fail(SR_EINVAL, "%s: %s is too large", fn, name);
+    return SR_OK;
+}
+
+struct Range {
+    uintptr_t lo, hi;
+};
+static Range span(const void *p, int64_t ld, int64_t rows, int64_t cols, sr_dtype t)
+{
+    const uintptr_t b = reinterpret_cast<uintptr_t>(p);
+    return {b, b + (uintptr_t)(((rows - 1) * ld + row_units(t, cols)) * esize(t))};
+}
+static bool overlap(Range a, Range b) { return a.lo < b.hi && b.lo < a.hi; }
+
+static bool vec_ok(sr_dtype t, std::initializer_list<std::pair<const void *, int64_t>> mats)
+{
+    for (auto &m : mats)
+        if (!aligned16(m.first) || ((m.second * esize(t)) & 15) != 0)
+            return false;
+    return true;
+}
+
+static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+void __attribute__((weak)) sr_ctx_shutdown(sr_ctx *) {}
+
+}  // namespace sr
+
+using namespace sr;
+
+// ======================================================================= API
+extern "C" {
+
+const char *sr_last_error(void) { return g_err.c_str(); }
+
+const char *sr_version(void) { return "semiring-gb300 0.1 (sm_103a)"; }
+
+sr_status sr_create(sr_ctx **out, const sr_config *cfg)
+{
+    if (!out)
+        return fail(SR_EINVAL, "sr_create: out is NULL");
+    *out = nullptr;
+    sr_ctx *c = new (std::nothrow) sr_ctx();
+    if (!c)
+        return fail(SR_ENOMEM, "sr_create: host allocation failed");
+    c->device = current_device();
+    if (cfg) {
+        c->ws_bytes = cfg->workspace_bytes;
+        c->spin_limit = cfg->spin_limit > 0 ? cfg->spin_limit : kDefaultSpinLimit;
+    }
+    cudaError_t e = cudaMalloc(&c->d_status, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "sr_create: cudaMalloc(status)");
+    }
+    e = cudaMemset(c->d_status, 0, sizeof(int) * 4);
+    if (e == cudaSuccess && c->ws_bytes) {
+        e = cudaMalloc(&c->ws, c->ws_bytes);
+        if (e != cudaSuccess) {
+            cudaFree(c->d_status);
+            delete c;
+            return fail(SR_ENOMEM, "sr_create: cannot allocate %zu workspace bytes (%s)", cfg->workspace_bytes,
+                        cudaGetErrorString(e));
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return cuda_fail(e, "sr_create");
+    }
+    *out = c;
+    return SR_OK;
+}
+
+void sr_destroy(sr_ctx *c)
+{
+    if (!c)
+        return;
+    sr_ctx_shutdown(c);
+    if (c->ws) cudaFree(c->ws);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+}
+
+sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size_t *bytes)
+{
+    if (!bytes)
+        return fail(SR_EINVAL, "sr_workspace_query: bytes is NULL");
+    *bytes = 0;
+    SR_TRY(check_dim("sr_workspace_query", "D", D));
+    if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_SQUARING) {
+        const int64_t rw = row_units(dtype, D) * u32_per_unit(dtype);
+        const int64_t ldw = (rw + 3) / 4 * 4;
+        *bytes = (size_t)(2 * D * ldw * 4);
+    }
+    return SR_OK;
+}
+
+sr_status sr_stream_status(sr_ctx *c, void *stream)
+{
+    if (!c)
+        return fail(SR_EINVAL, "sr_stream_status: ctx is NULL");
+    SR_CUDA_CHECK(cudaStreamSynchronize(S(stream)));
+    int h[4] = {0, 0, 0, 0};
+    SR_CUDA_CHECK(cudaMemcpy(h, c->d_status, sizeof h, cudaMemcpyDeviceToHost));
+    SR_CUDA_CHECK(cudaMemset(c->d_status, 0, sizeof h));
+    if (h[0])
+        return fail(SR_ETIMEOUT, "a bounded device-side wait gave up (code %d, where %d)", h[0], h[1]);
+    return SR_OK;
+}
+
+// ------------------------------------------------------------------ encoding
+sr_status antidist_encode(sr_ctx *, const void *W, int64_t ldw, void *T, int64_t ldt, int64_t R, int64_t C,
+                          sr_dtype dtype, void *stream)
+{
+    const char *fn = "antidist_encode";
+    if (!is_anti(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "C", C));
+    SR_TRY(check_mat(fn, "W", W, ldw, R, C, dtype));
+    SR_TRY(check_mat(fn, "T", T, ldt, R, C, dtype));
+    return launch_antidist_encode(W, ldw, T, ldt, (int)R, (int)C, dtype, device_sm_count(), S(stream));
+}
+
+sr_status bool_pack(sr_ctx *, const uint8_t *dense, int64_t ldd, void *M, int64_t ldm, int64_t R, int64_t C,
+                    sr_dtype dtype, void *stream)
+{
+    const char *fn = "bool_pack";
+    if (!is_bool(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "C", C));
+    SR_TRY(check_mat(fn, "dense", dense, ldd, R, C, SR_U8));
+    SR_TRY(check_mat(fn, "M", M, ldm, R, C, dtype));
+    const int rw = (int)(row_units(dtype, C) * u32_per_unit(dtype));
+    return launch_bool_pack(dense, ldd, static_cast<uint32_t *>(M), ldm * u32_per_unit(dtype), (int)R, (int)C, rw,
+                            device_sm_count(), S(stream));
+}
+
+sr_status bool_unpack(sr_ctx *, const void *M, int64_t ldm, uint8_t *dense, int64_t ldd, int64_t R, int64_t C,
+                      sr_dtype dtype, void *stream)
+{
+    const char *fn = "bool_unpack";
+    if (!is_bool(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "C", C));
+    SR_TRY(check_mat(fn, "M", M, ldm, R, C, dtype));
+    SR_TRY(check_mat(fn, "dense", dense, ldd, R, C, SR_U8));
+    return launch_bool_unpack(static_cast<const uint32_t *>(M), ldm * u32_per_unit(dtype), dense, ldd, (int)R,
+                              (int)C, device_sm_count(), S(stream));
+}
+
+// ------------------------------------------------------------------ products
+sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                       int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
+{
+    const char *fn = "antidist_mul";
+    if (!is_anti(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "K", K));
+    SR_TRY(check_dim(fn, "N", N));
+    SR_TRY(check_mat(fn, "A", A, lda, R, K, dtype));
+    SR_TRY(check_mat(fn, "B", B, ldb, K, N, dtype));
+    SR_TRY(check_mat(fn, "C", C, ldc, R, N, dtype));
+    const Range rc = span(C, ldc, R, N, dtype);
+    if (overlap(rc, span(A, lda, R, K, dtype)) || overlap(rc, span(B, ldb, K, N, dtype)))
+        return fail(SR_EINVAL, "%s: C overlaps A or B (use antidist_closure for the in-place form)", fn);
+    MulArgs a;
+    a.A = A; a.B = B; a.C = C;
+    a.lda = lda; a.ldb = ldb; a.ldc = ldc;
+    a.R = (int)R; a.K = (int)K; a.N = (int)N;
+    a.accumulate = accumulate ? 1 : 0;
+    a.skip0 = 0x7fffffff; a.skipw = 0;
+    const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
+    return launch_antidist_mul(a, dtype, vec, S(stream));
+}
+
+static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                               int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, cudaStream_t s)
+{
+    const int u = u32_per_unit(dtype);
+    BoolArgs a;
+    a.A = static_cast<const uint32_t *>(A);
+    a.B = static_cast<const uint32_t *>(B);
+    a.C = static_cast<uint32_t *>(C);
+    a.lda = lda * u; a.ldb = ldb * u; a.ldc = ldc * u;
+    a.R = (int)R; a.K = (int)K; a.N = (int)N;
+    a.ncw = (int)(row_units(dtype, N) * u);
+    a.accumulate = accumulate ? 1 : 0;
+    a.skip0 = 0x7fffffff; a.skipw = 0;
+    a.skip0w = 0x7fffffff; a.skipww = 0;
+    const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
+    return launch_bool_mul(a, vec, s);
+}
+
+sr_status bool_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                   int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
+{
+    const char *fn = "bool_mul";
+    if (!is_bool(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "K", K));
+    SR_TRY(check_dim(fn, "N", N));
+    SR_TRY(check_mat(fn, "A", A, lda, R, K, dtype));
+    SR_TRY(check_mat(fn, "B", B, ldb, K, N, dtype));
+    SR_TRY(check_mat(fn, "C", C, ldc, R, N, dtype));
+    const Range rc = span(C, ldc, R, N, dtype);
+    if (overlap(rc, span(A, lda, R, K, dtype)) || overlap(rc, span(B, ldb, K, N, dtype)))
+        return fail(SR_EINVAL, "%s: C overlaps A or B (use bool_closure for the in-place form)", fn);
+    return bool_mul_impl(A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate, S(stream));
+}
+
+// ------------------------------------------------------------------ closures
+sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
+{
+    const char *fn = "antidist_closure";
+    if (!is_anti(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+    SR_TRY(check_dim(fn, "D", D));
+    SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
+    const bool vec = vec_ok(dtype, {{T, ldt}});
+    return launch_antidist_closure(T, ldt, (int)D, dtype, vec, S(stream));
+}
+
+sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, int method, void *stream)
+{
+    const char *fn = "bool_closure";
+    if (!is_bool(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
+    SR_TRY(check_dim(fn, "D", D));
+    SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
+    const int u = u32_per_unit(dtype);
+    const int rw = (int)(row_units(dtype, D) * u);
+    const bool vec = vec_ok(dtype, {{T, ldt}});
+    uint32_t *T32 = static_cast<uint32_t *>(T);
+    if (method == SR_CLOSURE_WARSHALL)
+        return launch_bool_closure_warshall(T32, ldt * u, (int)D, rw, vec, S(stream));
+    if (method != SR_CLOSURE_SQUARING)
+        return fail(SR_EINVAL, "%s: unknown method %d", fn, method);
+    size_t need = 0;
+    SR_TRY(sr_workspace_query(SR_OP_BOOL_CLOSURE, dtype, D, method, &need));
+    if (!c)
+        return fail(SR_EINVAL, "%s: the squaring method needs a context with workspace", fn);
+    if (c->ws_bytes < need)
+        return fail(SR_ENOMEM, "%s: squaring needs %zu workspace bytes, context has %zu", fn, need, c->ws_bytes);
+    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words
+    const int64_t ldw = ((int64_t)rw + 3) / 4 * 4;
+    if ((size_t)(2 * D * ldw * 4) > c->ws_bytes)
+        return fail(SR_ENOMEM, "%s: workspace too small for padded rows", fn);
+    uint32_t *M = static_cast<uint32_t *>(c->ws);
+    uint32_t *M2 = M + D * ldw;
+    cudaStream_t s = S(stream);
+    SR_TRY(launch_copy_rows(T32, ldt * u, M, ldw, (int)D, rw, s));
+    SR_TRY(launch_bool_identity_or(M, ldw, (int)D, s));                  // M = I ⊕ A
+    int m = 0;
+    while (((int64_t)1 << m) < (D - 1 > 1 ? D - 1 : 1)) ++m;
+    auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z) -> sr_status {
+        BoolArgs a;
+        a.A = X; a.B = Y; a.C = Z;
+        a.lda = ldx; a.ldb = ldy; a.ldc = ldw;
+        a.R = (int)D; a.K = (int)D; a.N = (int)D;
+        a.ncw = rw;
+        a.accumulate = 0;
+        a.skip0 = 0x7fffffff; a.skipw = 0;
+        a.skip0w = 0x7fffffff; a.skipww = 0;
+        const bool v = aligned16(X) && aligned16(Y) && ((ldx & 3) == 0) && ((ldy & 3) == 0);
+        return launch_bool_mul(a, v, s);
+    };
+    for (int it = 0; it < m; ++it) {                                      // M := M ⊗ M
+        SR_TRY(mul32(M, ldw, M, ldw, M2));
+        uint32_t *t = M; M = M2; M2 = t;
+    }
+    SR_TRY(mul32(T32, ldt * u, M, ldw, M2));                              // A ⊗ (I ⊕ A)^(2^m)
+    return launch_copy_rows(M2, ldw, T32, ldt * u, (int)D, rw, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// Context object behind the opaque sr_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/semiring.h"
+
+namespace sr {
+constexpr int kDefaultSpinLimit = 1 << 22;
+struct ServeState;
+}  // namespace sr
+
+struct sr_ctx {
+    int device = 0;
+    void *ws = nullptr;           // device workspace (sr_config.workspace_bytes)
+    size_t ws_bytes = 0;
+    int *d_status = nullptr;      // device status words: [0] error code, [1] where
+    int spin_limit = sr::kDefaultSpinLimit;
+    sr::ServeState *serve = nullptr;
+};
+
+namespace sr {
+void sr_ctx_shutdown(sr_ctx *c);   // stops the serving loop if running
+}

@@ -1,0 +1,56 @@
+// Internal launcher interface between the C ABI (capi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/semiring.h"
+
+namespace sr {
+
+constexpr int kMaxDevices = 64;
+int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
+int device_sm_count();         // SMs of the current device (cached)
+
+// Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
+// and columns of B/C with logical index >= skip0 are shifted by skipw (the
+// closure's phase 3 excludes the pivot block's rows and columns this way).
+struct MulArgs {
+    const void *A;
+    const void *B;
+    void *C;
+    int64_t lda, ldb, ldc;     // elements (anti-distance) or 32-bit words (Boolean)
+    int R, K, N;               // logical sizes: anti-distance entries / Boolean bits
+    int accumulate;
+    int skip0, skipw;
+};
+
+sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s);
+sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s);
+sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ldt, int R, int C,
+                                 sr_dtype dt, int num_sms, cudaStream_t s);
+
+// Boolean kernels work on 32-bit words; a W64 matrix is the same bit layout
+// with twice as many 32-bit words per row (little-endian).
+struct BoolArgs {
+    const uint32_t *A;
+    const uint32_t *B;
+    uint32_t *C;
+    int64_t lda, ldb, ldc;     // 32-bit words
+    int R, K, N;               // rows; bits of k; bits per row of C (pad bits of C are written 0)
+    int ncw;                   // logical 32-bit words per row of C (and of B) to process
+    int accumulate;
+    int skip0, skipw;          // excluded row range (rows of A and C)
+    int skip0w, skipww;        // excluded word range (words of B and C)
+};
+sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s);
+sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
+sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
+                           int rw, int num_sms, cudaStream_t s);
+sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C,
+                             int num_sms, cudaStream_t s);
+sr_status launch_bool_identity_or(uint32_t *M, int64_t ldm, int D, cudaStream_t s);
+sr_status launch_copy_rows(const uint32_t *src, int64_t lds, uint32_t *dst, int64_t ldd, int R, int rw,
+                           cudaStream_t s);
+
+}  // namespace sr

@@ -1,0 +1,54 @@
+"""The C-ABI library loads and exports every function include/semiring.h
+declares (no GPU needed: nothing is called)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "semiring.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s*([A-Za-z_]\w*)\s*\([^;{]*\)\s*;", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1705_08743_gb300 import _capi
+    return _capi
+
+
+def test_header_parses():
+    names = declared_functions()
+    for must in ["antidist_mul", "antidist_closure", "bool_mul", "bool_closure", "sr_create"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(cdll, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if n not in lib.exported_symbols()]
+    assert not missing, missing
+
+
+def test_errors_without_device(lib):
+    # argument checks run before any CUDA call: a bad dtype is rejected on any host
+    st = lib.lib.antidist_mul(None, 1, 4, 1, 4, 2, 4, 4, 4, 4, 0, 0, None)
+    assert st == lib.SR_EINVAL
+    assert "dtype" in lib.last_error()
+    st = lib.lib.antidist_closure(None, None, 4, 4, lib.SR_U8, None)
+    assert st == lib.SR_EINVAL and "NULL" in lib.last_error()
+    st = lib.lib.bool_mul(None, 16, 1, 16, 1, 16, 1, 4, 4, 4, lib.SR_BOOL_W32, 0, None)
+    assert st == lib.SR_EINVAL and "overlap" in lib.last_error()

@@ -1,0 +1,171 @@
+"""Anti-distance product and closure on the GPU (through the C ABI) against
+the CPU oracle, element by element.  All arithmetic is integer: bit-exact."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import to_dev, to_host, sr_dtype_of
+
+pytestmark = pytest.mark.gpu
+
+S_OF = {np.uint8: 255, np.uint16: 65535}
+
+
+def rand_anti(rng, R, C, dt, density, lo=1):
+    S = S_OF[dt]
+    v = rng.integers(lo, S + 1, size=(R, C), dtype=np.int64)
+    return np.where(rng.random((R, C)) < density, v, 0).astype(dt)
+
+
+def gpu_mul(A, B, C0=None, pad=(0, 0, 0)):
+    import paper_1705_08743_gb300 as sr
+    dt = A.dtype.type
+    R, K = A.shape
+    N = B.shape[1]
+    Ad, Bd = to_dev(A, pad[0]), to_dev(B, pad[1])
+    Cd = to_dev(np.zeros((R, N), dt) if C0 is None else C0, pad[2])
+    sr.antidist_mul(None, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, sr_dtype_of(dt),
+                    0 if C0 is None else 1)
+    out = to_host(Cd, dt)
+    if pad[2]:
+        assert (out[:, N:] == 0xA5).all(), "wrote past the row width"
+    return out[:, :N]
+
+
+def gpu_closure(A, pad=0):
+    import paper_1705_08743_gb300 as sr
+    dt = A.dtype.type
+    D = A.shape[0]
+    Td = to_dev(A, pad)
+    sr.antidist_closure(None, Td, Td.shape[1], D, sr_dtype_of(dt))
+    return to_host(Td, dt)[:, :D]
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 13, 5), (128, 64, 128), (200, 300, 257),
+                                   (129, 33, 130), (513, 77, 1000), (64, 1, 64)])
+def test_mul_random(dt, shape):
+    R, K, N = shape
+    rng = np.random.default_rng(R * 7 + K * 3 + N)
+    S = S_OF[dt]
+    for dens, lo in [(0.5, 1), (0.9, S - S // 8)]:
+        A, B = rand_anti(rng, R, K, dt, dens, lo), rand_anti(rng, K, N, dt, dens, lo)
+        ref = oracle.mul(A, B, S)
+        assert np.array_equal(gpu_mul(A, B), ref)
+        C0 = rand_anti(rng, R, N, dt, 0.5)
+        assert np.array_equal(gpu_mul(A, B, C0), oracle.mul(A, B, S, C=C0))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_mul_unaligned_leading_dims(dt):
+    rng = np.random.default_rng(3)
+    A, B = rand_anti(rng, 70, 45, dt, 0.6), rand_anti(rng, 45, 99, dt, 0.6)
+    S = S_OF[dt]
+    assert np.array_equal(gpu_mul(A, B, pad=(3, 5, 7)), oracle.mul(A, B, S))
+    C0 = rand_anti(rng, 70, 99, dt, 0.4)
+    assert np.array_equal(gpu_mul(A, B, C0, pad=(16, 32, 9)), oracle.mul(A, B, S, C=C0))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_mul_special_matrices(dt):
+    S = S_OF[dt]
+    rng = np.random.default_rng(4)
+    n = 96
+    I = (np.eye(n) * S).astype(dt)
+    A = rand_anti(rng, n, n, dt, 0.5)
+    assert np.array_equal(gpu_mul(I, A), A)                       # identity
+    assert np.array_equal(gpu_mul(A, I), A)
+    Z = np.zeros((n, n), dt)
+    assert np.array_equal(gpu_mul(A, Z), Z)                       # zero absorbs
+    F = np.full((n, n), S, dt)
+    assert np.array_equal(gpu_mul(F, F), F)                       # all-S
+    ones = np.ones((n, n), dt)                                    # lengths S-1: saturate
+    assert np.array_equal(gpu_mul(ones, ones), oracle.mul(ones, ones, S))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("D", [1, 2, 31, 33, 63, 64, 65, 127, 129, 200, 333])
+def test_closure_random(dt, D):
+    rng = np.random.default_rng(D)
+    S = S_OF[dt]
+    for dens, lo in [(min(1.0, 3.0 / D), S - S // 6), (0.3, 1), (min(1.0, 1.2 / D), S - 3)]:
+        A = rand_anti(rng, D, D, dt, dens, lo)
+        assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_closure_unaligned_ld(dt):
+    rng = np.random.default_rng(8)
+    A = rand_anti(rng, 150, 150, dt, 0.05, S_OF[dt] - 40)
+    assert np.array_equal(gpu_closure(A, pad=5), oracle.warshall(A, S_OF[dt]))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_closure_edge_cases(dt):
+    S = S_OF[dt]
+    D = 300
+    Z = np.zeros((D, D), dt)
+    assert np.array_equal(gpu_closure(Z), Z)
+    F = np.full((D, D), S, dt)
+    assert np.array_equal(gpu_closure(F), F)
+    I = (np.eye(D) * S).astype(dt)
+    assert np.array_equal(gpu_closure(I), I)
+    # a single long chain 0 -> 1 -> ... -> D-1 -> 0 of length-1 edges: saturates for u8
+    C = np.zeros((D, D), dt)
+    for i in range(D):
+        C[i, (i + 1) % D] = S - 1
+    assert np.array_equal(gpu_closure(C), oracle.warshall(C, S))
+    # reversed chain (pivot order stress)
+    assert np.array_equal(gpu_closure(C.T.copy()), oracle.warshall(C.T.copy(), S))
+
+
+def test_encode_matches_oracle():
+    import torch
+    import paper_1705_08743_gb300 as sr
+    for dt, S in [(np.uint8, 255), (np.uint16, 65535)]:
+        rng = np.random.default_rng(1)
+        W = rng.integers(0, S + 1, size=(37, 101)).astype(dt)
+        W[0, :4] = [0, 1, S - 1, S]
+        Wd = to_dev(W)
+        Td = torch.empty_like(Wd)
+        sr.antidist_encode(None, Wd, 101, Td, 101, 37, 101, sr_dtype_of(dt))
+        assert np.array_equal(to_host(Td, dt), oracle.encode_antidist(W, S).astype(dt))
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_cfg2_closure_full_4096():
+    """Anti-distance closure D=4096 u8 (p=0.05, w ~ U{1..31}, seed 1): whole
+    matrix against the oracle's Warshall, plus sampled rows against the
+    oracle's single-source path search."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D = 4096
+    W = synth.cfg2_antidist(D=D, seed=1)
+    Wd = to_dev(W)
+    Td = torch.empty_like(Wd)
+    sr.antidist_encode(None, Wd, D, Td, D, D, D, sr.SR_U8)
+    sr.antidist_closure(None, Td, D, D, sr.SR_U8)
+    got = to_host(Td, np.uint8)
+    A = oracle.encode_antidist(W, 255)
+    ref = oracle.warshall(A, 255)
+    assert np.array_equal(got, ref)
+    for src in [0, 1, 777, 2048, 4095]:
+        assert np.array_equal(got[src], oracle.closure_row(A, src, 255))
+
+
+@pytest.mark.slow
+def test_cfg2_product_full_4096():
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D = 4096
+    A = oracle.encode_antidist(synth.cfg2_antidist(D=D, seed=1, s_edge=0), 255).astype(np.uint8)
+    B = oracle.encode_antidist(synth.cfg2_antidist(D=D, seed=1, s_edge=3), 255).astype(np.uint8)
+    Ad, Bd = to_dev(A), to_dev(B)
+    Cd = torch.zeros((D, D), dtype=torch.uint8, device="cuda")
+    sr.antidist_mul(None, Ad, D, Bd, D, Cd, D, D, D, D, sr.SR_U8, 0)
+    got = to_host(Cd, np.uint8)
+    ref = oracle.mul(A, B, 255)
+    assert np.array_equal(got, ref)

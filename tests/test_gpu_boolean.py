@@ -1,0 +1,173 @@
+"""Boolean (bit-packed) product, packing and closure on the GPU through the C
+ABI, against the CPU oracle; bit-exact."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_bool(rng, R, C, p):
+    return (rng.random((R, C)) < p).astype(np.uint8)
+
+
+def packed(dense, w):
+    """Oracle packing into 64-bit words; a W32 matrix is the same bytes viewed as uint32."""
+    M = oracle.pack_bits(dense)
+    return M if w == 64 else M.view(np.uint32)
+
+
+def unpacked(M, w, C):
+    M64 = np.ascontiguousarray(M).view(np.uint64)
+    return oracle.unpack_bits(M64, C)
+
+
+def gpu_bool_mul(A, B, K, N, w, C0=None, pad=(0, 0, 0)):
+    import paper_1705_08743_gb300 as sr
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    R = A.shape[0]
+    Ad, Bd = to_dev(A, pad[0]), to_dev(B, pad[1])
+    Cd = to_dev(np.zeros_like(packed(np.zeros((R, N), np.uint8), w)) if C0 is None else C0, pad[2])
+    sr.bool_mul(None, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, dt, 0 if C0 is None else 1)
+    out = to_host(Cd, np.uint64 if w == 64 else np.uint32)
+    return out[:, :A.shape[1] if False else out.shape[1] - pad[2]]
+
+
+@pytest.mark.parametrize("w", [32, 64])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 70, 129), (64, 64, 64), (33, 200, 65), (300, 517, 1000),
+                                   (129, 4096, 96)])
+def test_bool_mul_random(w, shape):
+    R, K, N = shape
+    rng = np.random.default_rng(R + K + N)
+    for p in [0.02, 0.3]:
+        A, B = rand_bool(rng, R, K, p), rand_bool(rng, K, N, p)
+        got = gpu_bool_mul(packed(A, w), packed(B, w), K, N, w)
+        assert np.array_equal(unpacked(got, w, N), oracle.mul(A, B, 1))
+        C0 = rand_bool(rng, R, N, 0.1)
+        got = gpu_bool_mul(packed(A, w), packed(B, w), K, N, w, C0=packed(C0, w))
+        assert np.array_equal(unpacked(got, w, N), np.maximum(C0, oracle.mul(A, B, 1)))
+        # pad bits written zero
+        if N % 64:
+            g64 = np.ascontiguousarray(got).view(np.uint64)
+            assert int((g64[:, -1] >> np.uint64(N % 64)).sum()) == 0
+
+
+@pytest.mark.parametrize("w", [32, 64])
+def test_bool_mul_garbage_pad_bits_and_unaligned(w):
+    rng = np.random.default_rng(5)
+    R, K, N = 77, 100, 90
+    A, B = rand_bool(rng, R, K, 0.1), rand_bool(rng, K, N, 0.1)
+    Ap, Bp = packed(A, w).copy(), packed(B, w).copy()
+    # set every pad bit of A and B: the product must ignore them
+    for M, n in [(Ap, K), (Bp, N)]:
+        M64 = M.view(np.uint64)
+        if n % 64:
+            M64[:, -1] |= ~np.uint64((1 << (n % 64)) - 1)
+    got = gpu_bool_mul(Ap, Bp, K, N, w, pad=(1, 3, 2))
+    assert np.array_equal(unpacked(got, w, N), oracle.mul(A, B, 1))
+
+
+@pytest.mark.parametrize("w", [32, 64])
+def test_pack_unpack(w):
+    import torch
+    import paper_1705_08743_gb300 as sr
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    rng = np.random.default_rng(6)
+    for (R, C) in [(1, 1), (3, 31), (5, 64), (17, 65), (40, 1000)]:
+        d = rand_bool(rng, R, C, 0.4)
+        d[d == 1] = rng.integers(1, 256, size=int(d.sum()))        # any nonzero byte is 1
+        dd = to_dev(d)
+        ref = packed((d != 0).astype(np.uint8), w)
+        Md = torch.zeros(ref.shape, dtype=torch.int64 if w == 64 else torch.int32, device="cuda")
+        sr.bool_pack(None, dd, C, Md, ref.shape[1], R, C, dt)
+        assert np.array_equal(to_host(Md, ref.dtype), ref)
+        back = torch.zeros((R, C), dtype=torch.uint8, device="cuda")
+        sr.bool_unpack(None, Md, ref.shape[1], back, C, R, C, dt)
+        assert np.array_equal(back.cpu().numpy(), (d != 0).astype(np.uint8))
+
+
+def gpu_bool_closure(dense, w, method, pad=0, ctx=None):
+    import paper_1705_08743_gb300 as sr
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    D = dense.shape[0]
+    Md = to_dev(packed(dense, w), pad)
+    sr.bool_closure(ctx, Md, Md.shape[1], D, dt, method)
+    out = to_host(Md, np.uint64 if w == 64 else np.uint32)
+    return out[:, :out.shape[1] - pad] if pad else out
+
+
+@pytest.fixture(scope="module")
+def sq_ctx():
+    import paper_1705_08743_gb300 as sr
+    ctx = sr.sr_create(workspace_bytes=64 << 20)
+    yield ctx
+    sr.sr_destroy(ctx)
+
+
+@pytest.mark.parametrize("w", [32, 64])
+@pytest.mark.parametrize("D", [1, 5, 31, 32, 33, 64, 65, 127, 128, 129, 200, 300, 513])
+def test_bool_closure(w, D, sq_ctx):
+    import paper_1705_08743_gb300 as sr
+    rng = np.random.default_rng(D * 3 + w)
+    for p in [1.5 / D, 0.5 / D, 4.0 / D]:
+        A = rand_bool(rng, D, D, min(1.0, p))
+        ref = oracle.warshall(A, 1)
+        for method in (sr.SR_CLOSURE_WARSHALL, sr.SR_CLOSURE_SQUARING):
+            got = gpu_bool_closure(A, w, method, ctx=sq_ctx)
+            assert np.array_equal(unpacked(got, w, D), ref), (p, method)
+
+
+def test_bool_closure_pad_and_unaligned(sq_ctx):
+    import paper_1705_08743_gb300 as sr
+    rng = np.random.default_rng(9)
+    D = 250
+    A = synth.bool_dag_union(D, seed=4)
+    ref = oracle.warshall(A, 1)
+    for w in (32, 64):
+        got = gpu_bool_closure(A, w, sr.SR_CLOSURE_WARSHALL, pad=3)
+        assert np.array_equal(unpacked(got, w, D), ref)
+
+
+def test_bool_squaring_needs_workspace():
+    import paper_1705_08743_gb300 as sr
+    A = np.zeros((40, 40), np.uint8)
+    with pytest.raises(sr.SemiringError) as e:
+        gpu_bool_closure(A, 64, sr.SR_CLOSURE_SQUARING, ctx=None)
+    assert e.value.status == sr.SR_EINVAL
+
+
+# ---------------------------------------------------------------- full size
+def test_cfg1_bool_product_512():
+    """512x512x512, Bernoulli(0.02), seed 0, 32 columns per word."""
+    A, B = synth.cfg1_bool_product()
+    got = gpu_bool_mul(packed(A, 32), packed(B, 32), 512, 512, 32)
+    ref = oracle.mul(A, B, 1)
+    assert np.array_equal(unpacked(got, 32, 512), ref)
+    assert 0.1 < ref.mean() < 0.3
+
+
+@pytest.mark.slow
+def test_cfg3_bool_closure_full_16384(sq_ctx):
+    """D=16384 W64 DAG-union graph, seed 2: Warshall form vs the oracle's
+    packed Warshall, and sampled rows by BFS; the squaring form on the same
+    input must agree (needs 2*32 MiB workspace)."""
+    import paper_1705_08743_gb300 as sr
+    D = 16384
+    G = synth.cfg3_bool_closure(D)
+    Gp = oracle.pack_bits(G)
+    ref = oracle.bool_warshall_w64(Gp)
+    got = gpu_bool_closure(G, 64, sr.SR_CLOSURE_WARSHALL)
+    assert np.array_equal(got, ref)
+    for src in [0, 5, 8191, 16383]:
+        assert np.array_equal(got[src], oracle.bool_closure_row_w64(Gp, src))
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, sr.SR_BOOL_W64, D,
+                                                              sr.SR_CLOSURE_SQUARING))
+    try:
+        got2 = gpu_bool_closure(G, 64, sr.SR_CLOSURE_SQUARING, ctx=ctx)
+    finally:
+        sr.sr_destroy(ctx)
+    assert np.array_equal(got2, ref)
