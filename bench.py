@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the semiring product/closure hot path on GB300.
+
+Default workload (one "step" = the whole hot path over one batch):
+  anti-distance closure D=4096 u8 (edge p=0.05, length U{1..31}, seed 1) plus
+  the product antidist_mul 4096x4096x4096 u8 (A = that graph, B = stream 3):
+  encode A -> T, encode A, encode B, closure(T) in place, C = A ⊗ B.
+  Metric: semiring ops per second, counting D^3 for the closure and R·K·N for
+  the product (2·4096^3 per step), in Gop/s.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+        [--workload cfg2|cfg2-8192|cfg1|cfg3|u16] [--no-cpu] [--no-e2e]
+Under torchrun each rank runs an independent replica on its own GPU (the
+closure does not shard without an exchange step; replicas only) and rank 0
+prints one JSON line with the max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "closure/product semiring Gop/s (D³/s) vs int-pipe peak; batched p50/p99 ms"
+UNIT = "Gop/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "mul", "closure"],
+                    help="profiling aid: run only one part of the step (not a bench line)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- ranks
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- workloads
+def sha_of(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_key: str, sources):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_sha") != sha_of(sources):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Cfg2:
+    """Anti-distance closure + product, D x D u8 (or u16)."""
+
+    def __init__(self, D=4096, dtype="u8"):
+        self.D, self.dtype = D, dtype
+        self.name = (f"antidist_closure D={D} {dtype} + antidist_mul {D}x{D}x{D} {dtype} "
+                     f"(edge p=0.05, length U{{1..31}}, seed 1; B: stream 3)")
+        self.ops = 2 * D ** 3
+
+    def host_inputs(self):
+        import numpy as np
+        import synth
+        npdt = np.uint8 if self.dtype == "u8" else np.uint16
+        WA = synth.cfg2_antidist(D=self.D, seed=1, s_edge=0, dtype=npdt)
+        WB = synth.cfg2_antidist(D=self.D, seed=1, s_edge=3, dtype=npdt)
+        return WA, WB
+
+    def setup_device(self, WA, WB, dev):
+        import torch
+        import paper_1705_08743_gb300 as sr
+        tdt = torch.uint8 if self.dtype == "u8" else torch.int16
+        self.sdt = sr.SR_U8 if self.dtype == "u8" else sr.SR_U16
+        view = (lambda a: a) if self.dtype == "u8" else (lambda a: a.view("int16"))
+        self.WA = torch.from_numpy(view(WA)).to(dev)
+        self.WB = torch.from_numpy(view(WB)).to(dev)
+        D = self.D
+        self.T = torch.empty((D, D), dtype=tdt, device=dev)
+        self.A = torch.empty_like(self.T)
+        self.B = torch.empty_like(self.T)
+        self.C = torch.empty_like(self.T)
+        self.mul_events = []
+        sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt)
+        sr.antidist_encode(None, self.WB, D, self.B, D, D, D, self.sdt)
+
+    only = ""
+
+    def step(self, stream, record_mul=False):
+        import torch
+        import paper_1705_08743_gb300 as sr
+        D, s = self.D, stream.cuda_stream
+        if self.only == "mul":
+            sr.antidist_mul(None, self.A, D, self.B, D, self.C, D, D, D, D, self.sdt, 0, s)
+            return
+        if self.only == "closure":
+            sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
+            sr.antidist_closure(None, self.T, D, D, self.sdt, s)
+            return
+        sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
+        sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt, s)
+        sr.antidist_encode(None, self.WB, D, self.B, D, D, D, self.sdt, s)
+        sr.antidist_closure(None, self.T, D, D, self.sdt, s)
+        if record_mul:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        sr.antidist_mul(None, self.A, D, self.B, D, self.C, D, D, D, D, self.sdt, 0, s)
+        if record_mul:
+            e1.record(stream)
+            self.mul_events.append((e0, e1))
+
+    # host-buffer path: H2D of both weight matrices, the step, D2H of T and C
+    def e2e_setup(self, WA, WB):
+        import torch
+        view = (lambda a: a) if self.dtype == "u8" else (lambda a: a.view("int16"))
+        self.hWA = torch.from_numpy(view(WA)).pin_memory()
+        self.hWB = torch.from_numpy(view(WB)).pin_memory()
+        self.hT = torch.empty(self.hWA.shape, dtype=self.hWA.dtype).pin_memory()
+        self.hC = torch.empty_like(self.hT).pin_memory()
+        self.h2d = 2 * self.hWA.numel() * self.hWA.element_size()
+        self.d2h = 2 * self.hT.numel() * self.hT.element_size()
+
+    def e2e_step(self, stream):
+        self.WA.copy_(self.hWA, non_blocking=True)
+        self.WB.copy_(self.hWB, non_blocking=True)
+        self.step(stream)
+        self.hT.copy_(self.T, non_blocking=True)
+        self.hC.copy_(self.C, non_blocking=True)
+
+    # roofline of the dominant kernel: the product kernel (also the closure's phase 3)
+    roofline_kernel = "antidist_mul_kernel<KindU8,128,128,32,8,16>"
+    roofline_sources = ["paper_1705_08743_gb300/csrc/antidist.cu", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
+
+    def cpu_sample(self, WA, WB):
+        """Oracle on a bounded sample: full closure at this D, product on the first rows."""
+        import numpy as np
+        import oracle
+        S = 255 if self.dtype == "u8" else 65535
+        D = self.D
+        rows = max(1, D // 4)
+        t0 = time.perf_counter()
+        A = oracle.encode_antidist(WA, S)
+        B = oracle.encode_antidist(WB, S)
+        oracle.warshall(A, S)
+        oracle.mul(A[:rows], B, S)
+        dt = time.perf_counter() - t0
+        ops = D ** 3 + rows * D * D
+        return {"ops": ops, "seconds": dt,
+                "sample": f"oracle encode + Warshall closure D={D} + product rows 0..{rows - 1} of {D}^3 "
+                          f"({ops / 1e9:.1f} Gop)"}
+
+
+WORKLOADS = {
+    "cfg2": lambda: Cfg2(4096, "u8"),
+    "cfg2-8192": lambda: Cfg2(8192, "u8"),
+    "u16": lambda: Cfg2(4096, "u16"),
+}
+
+
+# --------------------------------------------------------------------------- arms
+def run_reference(args, world, rank):
+    """The CPU oracle, as it stands, on the host cores; rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]()
+    WA, WB = wl.host_inputs()
+    for _ in range(args.warmup):
+        wl.cpu_sample(WA, WB)
+    times, sample = [], None
+    for _ in range(args.steps):
+        r = wl.cpu_sample(WA, WB)
+        times.append(r["seconds"])
+        sample = r
+    mean = sum(times) / len(times)
+    value = sample["ops"] / mean / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+        "config": {"workload": wl.name, "sample": sample["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1705_08743_gb300 as sr
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]()
+    wl.only = args.only
+    WA, WB = wl.host_inputs()
+
+    # CPU baseline first (rank 0, N = 1): before any GPU work of this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        r = wl.cpu_sample(WA, WB)
+        cpu = {"value": r["ops"] / r["seconds"] / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": r["sample"]}
+
+    wl.setup_device(WA, WB, dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # pipe peak of the product's inner operation, measured on this GPU now
+    with torch.cuda.stream(stream):
+        pk_ms, pk_ips, pk_ops = sr.sr_peak_probe(sr.SR_PEAK_DPX_S16X2 if wl.dtype == "u8" else sr.SR_PEAK_U16_PAIR,
+                                                 iters=8192, blocks_per_sm=8, stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            wl.step(stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    wl.mul_events = []
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = sr.sr_kernel_launches()
+    ev = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()                                   # L2 flush, outside the events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wl.step(stream, record_mul=True)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = sr.sr_kernel_launches() - launches0
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    mul_ms = [a.elapsed_time(b) for a, b in wl.mul_events]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / args.steps
+    value = world * wl.ops / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        wl.e2e_setup(WA, WB)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                wl.e2e_step(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ee = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                wl.e2e_step(stream)
+                e1.record(stream)
+                ee.append((e0, e1))
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ee), world) / args.steps
+        e2e = {"value": world * wl.ops / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h}
+
+    if rank != 0:
+        return
+    if args.only:
+        print(json.dumps({"only": args.only, "ms_per_step": ms_per_step, "gpu_launches": launches}), flush=True)
+        return
+    mul_avg = sum(mul_ms) / len(mul_ms)
+    achieved = wl.D ** 3 / (mul_avg * 1e-3) / 1e9
+    peak = pk_ops / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+        "config": {"workload": wl.name, "step": "encode x3 + closure (in place) + product",
+                   "ops_per_step": wl.ops, "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": wl.roofline_kernel, "achieved": achieved, "peak": peak,
+                     "unit": "Gop/s", "frac": achieved / peak,
+                     "peak_source": "measured now: issue-bound DPX add-max stream on all SMs (sr_peak_probe)",
+                     "launch_ms": mul_avg,
+                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources)},
+        "parts_ms": {"product": mul_avg, "closure_and_encode": ms_per_step - mul_avg},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

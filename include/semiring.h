@@ -145,6 +145,23 @@ sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dt
 
 /* ---------------------------------------------------------------- diagnostics */
 
+/* Number of kernel launches this library has made in this process (all devices). */
+uint64_t sr_kernel_launches(void);
+
+/* Roofline denominators: micro-benchmark of one inner operation of the
+ * kernels, as an issue-bound stream over every SM of the current device
+ * (blocks_per_sm CTAs of 256 threads, 128·iters operations per thread).
+ * Synchronises `stream`; allocates and frees a few bytes with cudaMallocAsync.
+ * Outputs: elapsed ms, instructions/s, semiring operations/s. */
+typedef enum {
+    SR_PEAK_DPX_S16X2 = 0,   /* max(x + a, acc) on 16-bit lane pairs (u8 product): 2 ops/instr */
+    SR_PEAK_U16_PAIR = 1,    /* max(max(x, na) + nga, acc) on lane pairs (u16): 2 ops per 2 instr */
+    SR_PEAK_LOP3 = 2,        /* acc |= x & m (Boolean): 32 ops/instr */
+    SR_PEAK_IADD = 3         /* 32-bit integer add (reference) */
+} sr_peak_op;
+sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *stream, double *ms,
+                        double *instr_per_s, double *ops_per_s);
+
 /* Reads and clears the context's device status word (bounded waits that gave
  * up), synchronising `stream` first.  SR_OK or SR_ETIMEOUT. */
 sr_status sr_stream_status(sr_ctx *ctx, void *stream);

@@ -28,6 +28,7 @@ SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ETIMEOUT, SR_EAGAIN, SR_EBUSY, SR_ENOT
 SR_BOOL_W32, SR_BOOL_W64, SR_U8, SR_U16 = range(4)
 SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
 SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
+SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD = range(4)
 
 STATUS_NAMES = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ETIMEOUT",
                 5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND"}
@@ -53,6 +54,9 @@ _SIGS = {
     "sr_version": (ctypes.c_char_p, []),
     "sr_workspace_query": (_st, [_int, _int, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "sr_stream_status": (_st, [_vp, _vp]),
+    "sr_kernel_launches": (ctypes.c_uint64, []),
+    "sr_peak_probe": (_st, [_int, _int, _int, _vp, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "antidist_encode": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
     "bool_pack": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
     "bool_unpack": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
@@ -125,6 +129,18 @@ def sr_workspace_query(op: int, dtype: int, D: int, method: int = 0) -> int:
 
 def sr_stream_status(ctx, stream=None):
     _check(lib.sr_stream_status(ctx, _stream(stream)), "sr_stream_status")
+
+
+def sr_kernel_launches() -> int:
+    return int(lib.sr_kernel_launches())
+
+
+def sr_peak_probe(op: int, iters: int = 4096, blocks_per_sm: int = 8, stream=None):
+    """-> (ms, instructions/s, semiring ops/s) of one inner operation on all SMs."""
+    ms, ips, ops = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.sr_peak_probe(op, iters, blocks_per_sm, _stream(stream), ctypes.byref(ms), ctypes.byref(ips),
+                             ctypes.byref(ops)), "sr_peak_probe")
+    return ms.value, ips.value, ops.value
 
 
 def antidist_encode(ctx, W, ldw, T, ldt, R, C, dtype, stream=None):

@@ -479,6 +479,7 @@ static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s)
     }
     kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -505,6 +506,7 @@ static sr_status launch_panel(void *T, int64_t ldt, int D, int kb, cudaStream_t 
     }
     antidist_panel_kernel<KD, PB><<<2 * nb - 1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -567,6 +569,7 @@ sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ld
         antidist_encode_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(W), ldw,
                                                                static_cast<uint16_t *>(T), ldt, R, C, 65535u);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 

@@ -351,6 +351,7 @@ static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
     }
     kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -367,10 +368,12 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
     const int nb = (D + PB - 1) / PB;
     bool_clear_pad_kernel<<<(D + 255) / 256, 256, 0, s>>>(T, ldt, D, D, rw);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     for (int kb = 0; kb < nb; ++kb) {
         const int k0 = kb * PB, bw = std::min(PB, D - k0);
         bool_panel_kernel<PB><<<2 * nb - 1, PB, 0, s>>>(T, ldt, D, rw, kb);
         SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
         if (nb > 1) {
             BoolArgs a;
             a.A = T + k0 / 32;
@@ -405,6 +408,7 @@ sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 7) / 8, (int64_t)num_sms * 16));
     bool_pack_kernel<<<blocks, 256, 0, s>>>(dense, ldd, M, ldm, R, C, rw);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -415,6 +419,7 @@ sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
     bool_unpack_kernel<<<blocks, 256, 0, s>>>(M, ldm, dense, ldd, R, C);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -422,6 +427,7 @@ sr_status launch_bool_identity_or(uint32_t *M, int64_t ldm, int D, cudaStream_t 
 {
     bool_identity_or_kernel<<<(D + 255) / 256, 256, 0, s>>>(M, ldm, D);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 
@@ -432,6 +438,7 @@ sr_status launch_copy_rows(const uint32_t *src, int64_t lds, uint32_t *dst, int6
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
     copy_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, dst, ldd, R, rw);
     SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
     return SR_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -41,6 +42,9 @@ sr_status cuda_fail(cudaError_t e, const char *what)
     g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return SR_ECUDA;
 }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 int current_device()
 {
@@ -127,6 +131,8 @@ extern "C" {
 const char *sr_last_error(void) { return g_err.c_str(); }
 
 const char *sr_version(void) { return "semiring-gb300 0.1 (sm_103a)"; }
+
+uint64_t sr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 sr_status sr_create(sr_ctx **out, const sr_config *cfg)
 {

@@ -11,6 +11,7 @@ namespace sr {
 constexpr int kMaxDevices = 64;
 int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
+void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
 // and columns of B/C with logical index >= skip0 are shifted by skipw (the
