@@ -143,6 +143,28 @@ sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtyp
 sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
                        int method, void *stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Size of the library-owned scratch array used by bool_closure_squaring_noalloc. */
+#define SR_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Boolean closure by repeated squaring, like bool_closure(..., SR_CLOSURE_SQUARING, ...),
+ * but with no workspace argument and no allocation of any kind.  (The paper has no
+ * counterpart: this is a deployment variant of the library.)  It is for callers that
+ * cannot allocate device memory — code that runs where another allocator already owns
+ * the device's memory, plugins held to a fixed memory budget, loops that must not pay
+ * for cudaMalloc's implicit synchronisation.  Its scratch is a 16 MiB array inside the
+ * library image, present on every GPU that loads the library until the process exits.
+ *  - T, ldt, D, dtype as in bool_closure; D×D problems whose two scratch matrices
+ *    (2·D·ceil32(D)/8 bytes, rows padded to 16 bytes) exceed SR_NOALLOC_SCRATCH_BYTES
+ *    return SR_EINVAL before anything is queued; every D <= 8192 fits.
+ *  - All calls share the one array and leave their data in it; each call overwrites
+ *    the scratch it reads, but calls that overlap on the GPU (unordered streams) race.
+ *  - The first call on a device looks the array's address up on that device; make that
+ *    first call before any stream capture.
+ *  - Calls no cudaMalloc/cudaFree or any allocating routine. */
+sr_status bool_closure_squaring_noalloc(void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Number of kernel launches this library has made in this process (all devices). */

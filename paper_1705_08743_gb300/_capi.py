@@ -64,6 +64,7 @@ _SIGS = {
     "bool_mul": (_st, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp]),
     "antidist_closure": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
     "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
+    "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -171,3 +172,12 @@ def antidist_closure(ctx, T, ldt, D, dtype, stream=None):
 
 def bool_closure(ctx, T, ldt, D, dtype, method=SR_CLOSURE_WARSHALL, stream=None):
     _check(lib.bool_closure(ctx, _ptr(T), ldt, D, dtype, method, _stream(stream)), "bool_closure")
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def bool_closure_squaring_noalloc(T, ldt, D, dtype, stream=None):
+    """Allocation-free Boolean closure by squaring (library-owned 16 MiB scratch)."""
+    _check(lib.bool_closure_squaring_noalloc(_ptr(T), ldt, D, dtype, _stream(stream)),
+           "bool_closure_squaring_noalloc")
