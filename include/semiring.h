@@ -143,6 +143,51 @@ sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtyp
 sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
                        int method, void *stream);
 
+/* ---------------------------------------------------------------- batched closures (many graphs, one launch) */
+
+/* One operation of a batch or a served request.  Closures: C is the D×D matrix
+ * closed in place, ldc its leading dimension, R = K = N = D (A, B unused).
+ * Products: C := (accumulate ? C : 0) ⊕ A ⊗ B with A R×K, B K×N (lda/ldb/ldc as in
+ * the product calls).  All pointers are device pointers owned by the caller. */
+typedef struct {
+    int op;                /* sr_op */
+    int dtype;             /* sr_dtype */
+    const void *A;
+    const void *B;
+    void *C;
+    int64_t lda, ldb, ldc;
+    int64_t R, K, N;
+    int accumulate;
+    int method;            /* closures of Boolean matrices: sr_closure_method */
+} sr_desc;
+
+typedef struct sr_batch sr_batch;
+
+/* Plan a batch of n independent anti-distance closures (op SR_OP_ANTIDIST_CLOSURE,
+ * one dtype for the whole batch, matrices must not overlap) for one persistent
+ * launch (Section 2 Warshall / Section 3 Floyd on every graph).  Graphs are ordered
+ * by cost, largest first; graphs with D >= the cooperative threshold are closed by
+ * all CTAs of a thread-block cluster together, smaller ones one per CTA.  Allocates
+ * the plan's small device arrays (descriptors, work items, one counter). */
+sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out);
+/* Enqueue the batch on `stream`.  use_graph != 0: the counter reset and the
+ * persistent kernel are captured once into a CUDA graph, replayed on every later call. */
+sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream);
+/* Tuning: cluster size (1, 2 or 4), cooperative threshold on D, CTAs per SM. */
+sr_status sr_batch_set_tuning(sr_batch *b, int cluster, int coop_threshold, int ctas_per_sm);
+sr_status sr_batch_get_tuning(const sr_batch *b, int *cluster, int *coop_threshold, int *ctas_per_sm);
+/* Autotuner: times the candidate tunings on this batch (closures are idempotent, so
+ * re-running them leaves the results unchanged), keeps the fastest, and records it in
+ * ctx under the batch's signature (dtype, SM count, histogram of D); a later call with
+ * a batch of the same signature reuses it without timing.  Synchronises `stream`.
+ * best_ms (may be NULL) receives the best time per launch, or -1 if reused. */
+sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, double *best_ms);
+sr_status sr_batch_info(const sr_batch *b, int *ngraphs, int *nitems, double *ops);
+void sr_batch_destroy(sr_batch *b);
+/* One-shot form: plan (using ctx's recorded tuning for this signature, if any),
+ * launch, synchronise `stream`, free the plan. */
+sr_status sr_batched(sr_ctx *ctx, const sr_desc *d, int n, void *stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the library-owned scratch array used by bool_closure_squaring_noalloc. */

@@ -47,6 +47,13 @@ class sr_config(ctypes.Structure):
 
 _vp, _i64, _int, _st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int
 
+
+class sr_desc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("dtype", ctypes.c_int), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("R", ctypes.c_int64), ("K", ctypes.c_int64), ("N", ctypes.c_int64), ("accumulate", ctypes.c_int),
+                ("method", ctypes.c_int)]
+
 _SIGS = {
     "sr_create": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(sr_config)]),
     "sr_destroy": (None, [_vp]),
@@ -65,6 +72,14 @@ _SIGS = {
     "antidist_closure": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
     "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
     "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
+    "sr_batch_create": (_st, [_vp, ctypes.POINTER(sr_desc), _int, ctypes.POINTER(_vp)]),
+    "sr_batch_launch": (_st, [_vp, _int, _vp]),
+    "sr_batch_set_tuning": (_st, [_vp, _int, _int, _int]),
+    "sr_batch_get_tuning": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "sr_batch_autotune": (_st, [_vp, _vp, _vp, _int, ctypes.POINTER(ctypes.c_double)]),
+    "sr_batch_info": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
+    "sr_batch_destroy": (None, [_vp]),
+    "sr_batched": (_st, [_vp, ctypes.POINTER(sr_desc), _int, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -181,3 +196,56 @@ def bool_closure_squaring_noalloc(T, ldt, D, dtype, stream=None):
     """Allocation-free Boolean closure by squaring (library-owned 16 MiB scratch)."""
     _check(lib.bool_closure_squaring_noalloc(_ptr(T), ldt, D, dtype, _stream(stream)),
            "bool_closure_squaring_noalloc")
+
+
+def closure_desc(T, ldt, D, dtype):
+    """sr_desc of an in-place anti-distance closure."""
+    return sr_desc(op=SR_OP_ANTIDIST_CLOSURE, dtype=dtype, A=None, B=None, C=_ptr(T), lda=0, ldb=0, ldc=ldt,
+                   R=D, K=D, N=D, accumulate=0, method=0)
+
+
+def _desc_array(descs):
+    arr = (sr_desc * len(descs))(*descs)
+    return arr
+
+
+def sr_batch_create(ctx, descs):
+    arr = _desc_array(descs)
+    h = _vp()
+    _check(lib.sr_batch_create(ctx, arr, len(descs), ctypes.byref(h)), "sr_batch_create")
+    return h.value
+
+
+def sr_batch_launch(batch, use_graph=0, stream=None):
+    _check(lib.sr_batch_launch(batch, int(use_graph), _stream(stream)), "sr_batch_launch")
+
+
+def sr_batch_set_tuning(batch, cluster, coop_threshold, ctas_per_sm):
+    _check(lib.sr_batch_set_tuning(batch, cluster, coop_threshold, ctas_per_sm), "sr_batch_set_tuning")
+
+
+def sr_batch_get_tuning(batch):
+    a, b, c = _int(), _int(), _int()
+    _check(lib.sr_batch_get_tuning(batch, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sr_batch_get_tuning")
+    return a.value, b.value, c.value
+
+
+def sr_batch_autotune(ctx, batch, stream=None, reps=2):
+    ms = ctypes.c_double()
+    _check(lib.sr_batch_autotune(ctx, batch, _stream(stream), reps, ctypes.byref(ms)), "sr_batch_autotune")
+    return ms.value
+
+
+def sr_batch_info(batch):
+    n, it, ops = _int(), _int(), ctypes.c_double()
+    _check(lib.sr_batch_info(batch, ctypes.byref(n), ctypes.byref(it), ctypes.byref(ops)), "sr_batch_info")
+    return n.value, it.value, ops.value
+
+
+def sr_batch_destroy(batch):
+    lib.sr_batch_destroy(batch)
+
+
+def sr_batched(ctx, descs, stream=None):
+    arr = _desc_array(descs)
+    _check(lib.sr_batched(ctx, arr, len(descs), _stream(stream)), "sr_batched")

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <array>
+#include <map>
+#include <string>
+
 #include "../../include/semiring.h"
 
 namespace sr {
@@ -18,6 +22,7 @@ struct sr_ctx {
     int *d_status = nullptr;      // device status words: [0] error code, [1] where
     int spin_limit = sr::kDefaultSpinLimit;
     sr::ServeState *serve = nullptr;
+    std::map<std::string, std::array<int, 3>> tune;   // autotuned batch configurations by signature
 };
 
 namespace sr {
