@@ -188,6 +188,77 @@ void sr_batch_destroy(sr_batch *b);
  * launch, synchronise `stream`, free the plan. */
 sr_status sr_batched(sr_ctx *ctx, const sr_desc *d, int n, void *stream);
 
+/* ---------------------------------------------------------------- served request loop */
+
+/* One request of the serving loop.  Matrices are host buffers, dense row-major
+ * (leading dimension = row width, in entries or Boolean words), or resident
+ * matrices named by a handle.  For overlap and asynchrony the host buffers should
+ * be page-locked (cudaHostAlloc, torch pin_memory); pageable buffers still work but
+ * serialise the loop.  Inputs must stay valid and outputs untouched until the
+ * request is done.
+ *  - closures (SR_OP_ANTIDIST_CLOSURE u8/u16, SR_OP_BOOL_CLOSURE W32/W64 with
+ *    `method`): D = R; input A (or resident rA); result written to `out`.
+ *  - products (SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL): A R×K (or rA), B K×N (or rB),
+ *    result R×N written to `out` (NULL: no transfer back).
+ *  - keep != 0: the result stays resident; sr_result reports its handle. */
+typedef struct {
+    int op;
+    int dtype;
+    int64_t R, K, N;
+    const void *A;
+    const void *B;
+    uint64_t rA, rB;
+    void *out;
+    int keep;
+    int method;
+} sr_request;
+
+typedef struct {
+    size_t arena_bytes;      /* device memory budget for admitted requests and resident matrices (default 1 GiB) */
+    int slots;               /* concurrent stream slots: admitted work in flight (default 4) */
+    int max_pending;         /* waiting requests before sr_submit answers SR_EAGAIN (default 4096) */
+    int batch_max_d;         /* anti-distance closures with D <= this are grouped into one batched launch (512) */
+    int batch_max_graphs;    /* graphs per grouped launch (64, at most 1024) */
+    int backfill_ms;         /* later requests may overtake the head while it has waited less than this (0) */
+} sr_serve_config;
+
+typedef struct {
+    int status;              /* SR_OK, or the error that ended this request */
+    double latency_ms;       /* submission to completion (host clock) */
+    double queue_ms;         /* submission to admission */
+    uint64_t resident;       /* handle of the kept result (keep != 0), else 0 */
+} sr_result_info;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches, batched_requests;
+    size_t arena_bytes, arena_in_use, arena_peak_bytes;
+    int pending, inflight, residents;
+} sr_serve_stats_t;
+
+/* Start the loop on ctx's device: allocates the arena (one cudaMalloc), per-slot
+ * streams and staging buffers, and a scheduler thread.  Requests are admitted in
+ * submission order as stream slots and arena memory free up (continuous
+ * batching); waiting small closures of one dtype join one batched launch. */
+sr_status sr_serve_start(sr_ctx *ctx, const sr_serve_config *cfg);
+/* Stop the loop (waits for admitted work), free its memory; also done by sr_destroy. */
+sr_status sr_serve_stop(sr_ctx *ctx);
+/* Queue a request; returns its ticket.  SR_EAGAIN: queue full; SR_ENOMEM: larger
+ * than the whole arena; SR_EINVAL / SR_ENOTFOUND: bad request / unknown handle. */
+sr_status sr_submit(sr_ctx *ctx, const sr_request *req, uint64_t *ticket);
+sr_status sr_poll(sr_ctx *ctx, uint64_t ticket, int *done);
+/* Block until done or timeout_ms elapsed (SR_ETIMEOUT); returns the request's status. */
+sr_status sr_wait(sr_ctx *ctx, uint64_t ticket, int timeout_ms);
+sr_status sr_result(sr_ctx *ctx, uint64_t ticket, sr_result_info *info);
+/* Forget a finished ticket (a kept result stays resident until sr_resident_free). */
+sr_status sr_release(sr_ctx *ctx, uint64_t ticket);
+/* Resident matrices (in the arena): upload (blocking), download (synchronises the
+ * device first), free. */
+sr_status sr_resident_put(sr_ctx *ctx, const void *host, int64_t rows, int64_t cols, sr_dtype dtype,
+                          uint64_t *handle);
+sr_status sr_resident_get(sr_ctx *ctx, uint64_t handle, void *host);
+sr_status sr_resident_free(sr_ctx *ctx, uint64_t handle);
+sr_status sr_serve_stats(sr_ctx *ctx, sr_serve_stats_t *out);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the library-owned scratch array used by bool_closure_squaring_noalloc. */

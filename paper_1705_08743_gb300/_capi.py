@@ -54,6 +54,30 @@ class sr_desc(ctypes.Structure):
                 ("R", ctypes.c_int64), ("K", ctypes.c_int64), ("N", ctypes.c_int64), ("accumulate", ctypes.c_int),
                 ("method", ctypes.c_int)]
 
+class sr_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("dtype", ctypes.c_int), ("R", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("N", ctypes.c_int64), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("rA", ctypes.c_uint64),
+                ("rB", ctypes.c_uint64), ("out", ctypes.c_void_p), ("keep", ctypes.c_int), ("method", ctypes.c_int)]
+
+
+class sr_serve_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("slots", ctypes.c_int), ("max_pending", ctypes.c_int),
+                ("batch_max_d", ctypes.c_int), ("batch_max_graphs", ctypes.c_int), ("backfill_ms", ctypes.c_int)]
+
+
+class sr_result_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("resident", ctypes.c_uint64)]
+
+
+class sr_serve_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("batched_requests", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_size_t), ("arena_in_use", ctypes.c_size_t),
+                ("arena_peak_bytes", ctypes.c_size_t), ("pending", ctypes.c_int), ("inflight", ctypes.c_int),
+                ("residents", ctypes.c_int)]
+
+
 _SIGS = {
     "sr_create": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(sr_config)]),
     "sr_destroy": (None, [_vp]),
@@ -80,6 +104,17 @@ _SIGS = {
     "sr_batch_info": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
     "sr_batch_destroy": (None, [_vp]),
     "sr_batched": (_st, [_vp, ctypes.POINTER(sr_desc), _int, _vp]),
+    "sr_serve_start": (_st, [_vp, ctypes.POINTER(sr_serve_config)]),
+    "sr_serve_stop": (_st, [_vp]),
+    "sr_submit": (_st, [_vp, ctypes.POINTER(sr_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "sr_poll": (_st, [_vp, ctypes.c_uint64, ctypes.POINTER(_int)]),
+    "sr_wait": (_st, [_vp, ctypes.c_uint64, _int]),
+    "sr_result": (_st, [_vp, ctypes.c_uint64, ctypes.POINTER(sr_result_info)]),
+    "sr_release": (_st, [_vp, ctypes.c_uint64]),
+    "sr_resident_put": (_st, [_vp, _vp, _i64, _i64, _int, ctypes.POINTER(ctypes.c_uint64)]),
+    "sr_resident_get": (_st, [_vp, ctypes.c_uint64, _vp]),
+    "sr_resident_free": (_st, [_vp, ctypes.c_uint64]),
+    "sr_serve_stats": (_st, [_vp, ctypes.POINTER(sr_serve_stats_t)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -249,3 +284,76 @@ def sr_batch_destroy(batch):
 def sr_batched(ctx, descs, stream=None):
     arr = _desc_array(descs)
     _check(lib.sr_batched(ctx, arr, len(descs), _stream(stream)), "sr_batched")
+
+
+def _hptr(x):
+    """Host pointer of a numpy array or a (pinned) CPU torch tensor."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def sr_serve_start(ctx, arena_bytes=1 << 30, slots=4, max_pending=4096, batch_max_d=512, batch_max_graphs=64,
+                   backfill_ms=0):
+    cfg = sr_serve_config(arena_bytes=arena_bytes, slots=slots, max_pending=max_pending, batch_max_d=batch_max_d,
+                          batch_max_graphs=batch_max_graphs, backfill_ms=backfill_ms)
+    _check(lib.sr_serve_start(ctx, ctypes.byref(cfg)), "sr_serve_start")
+
+
+def sr_serve_stop(ctx):
+    _check(lib.sr_serve_stop(ctx), "sr_serve_stop")
+
+
+def make_request(op, dtype, R, K=0, N=0, A=None, B=None, rA=0, rB=0, out=None, keep=0, method=0):
+    return sr_request(op=op, dtype=dtype, R=R, K=K or R, N=N or R, A=_hptr(A), B=_hptr(B), rA=rA, rB=rB,
+                      out=_hptr(out), keep=keep, method=method)
+
+
+def sr_submit(ctx, req):
+    t = ctypes.c_uint64()
+    _check(lib.sr_submit(ctx, ctypes.byref(req), ctypes.byref(t)), "sr_submit")
+    return t.value
+
+
+def sr_poll(ctx, ticket):
+    d = _int()
+    _check(lib.sr_poll(ctx, ticket, ctypes.byref(d)), "sr_poll")
+    return bool(d.value)
+
+
+def sr_wait(ctx, ticket, timeout_ms=60000):
+    _check(lib.sr_wait(ctx, ticket, timeout_ms), "sr_wait")
+
+
+def sr_result(ctx, ticket):
+    info = sr_result_info()
+    _check(lib.sr_result(ctx, ticket, ctypes.byref(info)), "sr_result")
+    return info
+
+
+def sr_release(ctx, ticket):
+    _check(lib.sr_release(ctx, ticket), "sr_release")
+
+
+def sr_resident_put(ctx, host, rows, cols, dtype):
+    h = ctypes.c_uint64()
+    _check(lib.sr_resident_put(ctx, _hptr(host), rows, cols, dtype, ctypes.byref(h)), "sr_resident_put")
+    return h.value
+
+
+def sr_resident_get(ctx, handle, host):
+    _check(lib.sr_resident_get(ctx, handle, _hptr(host)), "sr_resident_get")
+
+
+def sr_resident_free(ctx, handle):
+    _check(lib.sr_resident_free(ctx, handle), "sr_resident_free")
+
+
+def sr_serve_stats(ctx):
+    st = sr_serve_stats_t()
+    _check(lib.sr_serve_stats(ctx, ctypes.byref(st)), "sr_serve_stats")
+    return {f: getattr(st, f) for f, _ in sr_serve_stats_t._fields_}

@@ -34,19 +34,6 @@ namespace cg = cooperative_groups;
 
 namespace sr {
 
-struct BatchGraph {
-    void *T;
-    int64_t ldt;
-    int D;
-    int pad;        // 1: T and every row are 16-byte aligned (vector accesses)
-};
-
-struct BatchItem {
-    int n;          // graphs in the item (1 for a cooperative item)
-    int coop;       // 1: all CTAs of the cluster close g[0] together
-    int g[4];
-};
-
 // Two register layouts of a PB×PB block for 128 threads, thread (r0, c0) with
 // r0 = tid / 8 in [0,16) and c0 = tid % 8; both hold rows r0 + 16 j (j < PB/16):
 //  - layout S (pivot closure): lane-pair columns c0 + 8 m.  Pivot kk = 16 j + q is
@@ -472,6 +459,23 @@ static sr_status launch_batched_nc(BatchPlan &p, cudaStream_t s)
                                      p.nitems, p.d_counter));
     count_launches();
     return SR_OK;
+}
+
+sr_status launch_batched_closure_flat(sr_dtype dt, const BatchGraph *d_graphs, const BatchItem *d_items, int nitems,
+                                      int *d_counter, int ctas_per_sm, cudaStream_t s)
+{
+    BatchPlan p;
+    p.dtype = dt;
+    p.nc = 1;
+    p.ctas_per_sm = ctas_per_sm;
+    p.nitems = nitems;
+    p.d_graphs = const_cast<BatchGraph *>(d_graphs);
+    p.d_items = const_cast<BatchItem *>(d_items);
+    p.d_counter = d_counter;
+    SR_CUDA_CHECK(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
+    const sr_status st = dt == SR_U8 ? launch_batched_nc<KindU8, 1>(p, s) : launch_batched_nc<KindU16, 1>(p, s);
+    p.d_graphs = nullptr; p.d_items = nullptr; p.d_counter = nullptr;   // not owned
+    return st;
 }
 
 static sr_status enqueue_batch(BatchPlan &p, cudaStream_t s)

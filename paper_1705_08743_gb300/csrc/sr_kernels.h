@@ -54,4 +54,20 @@ sr_status launch_bool_identity_or(uint32_t *M, int64_t ldm, int D, cudaStream_t 
 sr_status launch_copy_rows(const uint32_t *src, int64_t lds, uint32_t *dst, int64_t ldd, int R, int rw,
                            cudaStream_t s);
 
+// Batched closure (batched.cu): graph descriptors and work items on the device.
+struct BatchGraph {
+    void *T;
+    int64_t ldt;
+    int D;
+    int pad;        // 1: T and every row are 16-byte aligned (vector accesses)
+};
+struct BatchItem {
+    int n;          // graphs in the item (1 for a cooperative item)
+    int coop;       // 1: all CTAs of the cluster close g[0] together
+    int g[4];
+};
+// One persistent launch without clusters: item i closes graph items[i].g[0] on one CTA.
+sr_status launch_batched_closure_flat(sr_dtype dt, const BatchGraph *d_graphs, const BatchItem *d_items, int nitems,
+                                      int *d_counter, int ctas_per_sm, cudaStream_t s);
+
 }  // namespace sr
