@@ -18,11 +18,14 @@
 //            with K = PB, panel rows/columns excluded).
 // Every pivot order gives the same fixed point, and rows/columns of the pivot
 // block do not change in their own step, so the blocked order is exact.
-// Phases 1 and 2 run fused in one launch: each panel CTA closes the diagonal
-// block itself (all CTAs of the launch compute the identical T_kk).
+// Phase 1 runs on one CTA (the pivot block closed in registers); phase 2 is two
+// in-place products; a one-block look-ahead overlaps the next pivot's phases 1-2
+// with the current phase 3 (see closure_impl).
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
@@ -77,7 +80,8 @@ struct MulCfg {
     static constexpr int NP = TN / 2;
     static constexpr int A_CHUNKS = BM * BK / CH / THREADS;
     static constexpr int B_CHUNKS = BK * BN / CH / THREADS;
-    static constexpr size_t SMEM = (size_t)2 * BK * (KD::AW * BM + BN / 2) * sizeof(uint32_t);
+    static constexpr size_t SMEM = (size_t)2 * BK * (KD::AW * BM + BN / 2) * sizeof(uint32_t)
+                                   + (size_t)BM * BN * sizeof(E);                 // prefetched C tile
     static_assert(TM % 4 == 0 && TN % 8 == 0, "thread tile");
     static_assert(BK % CH == 0 && BN % CH == 0, "chunking");
     static_assert(A_CHUNKS * CH * THREADS == BM * BK && B_CHUNKS * CH * THREADS == BK * BN, "chunks");
@@ -92,11 +96,13 @@ antidist_mul_kernel(MulArgs p)
     using E = typename KD::elem;
     constexpr int TR = Cfg::TR, TC = Cfg::TC, THREADS = Cfg::THREADS, CH = Cfg::CH, NP = Cfg::NP;
     constexpr int BN2 = BN / 2;
+    constexpr int CROW = BN * (int)sizeof(E) / 16;        // 16-byte chunks per C tile row
 
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA0 = smem;                               // [2][BK][BM]  broadcast word 0
     uint32_t *sA1 = smem + 2 * BK * BM;                 // [2][BK][BM]  broadcast word 1 (u16)
     uint32_t *sB = smem + KD::AW * 2 * BK * BM;          // [2][BK][BN/2] lane pairs
+    uint4 *sC = reinterpret_cast<uint4 *>(sB + 2 * BK * BN2);   // [BM][CROW] prefetched C tile (raw)
 
     const E *__restrict__ A = static_cast<const E *>(p.A);
     const E *__restrict__ B = static_cast<const E *>(p.B);
@@ -104,60 +110,27 @@ antidist_mul_kernel(MulArgs p)
 
     const int tid = threadIdx.x;
     const int tc = tid % TC, tr = tid / TC;
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    const int tiles_n = (p.N + BN - 1) / BN, tiles = tiles_n * ((p.R + BM - 1) / BM);
+    const int nkt = (p.K + BK - 1) / BK;
 
-    uint32_t acc[TM][NP];
+    // tiles in row-major order; a persistent grid (gridDim.x < tiles) walks them round-robin
+    auto advance = [&](int t) {
+        t += gridDim.x;
+        if (t == p.skip_tile) t += gridDim.x;
+        return t;
+    };
+    int tile = blockIdx.x;
+    if (tile == p.skip_tile) tile = advance(tile);
 
-    // ---- initial accumulator: C tile or the semiring zero
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
-#pragma unroll
-        for (int g = 0; g < NP / 4; ++g) {
-            const int c = col0 + g * (8 * TC) + tc * 8;
-            uint32_t q[4] = {0u, 0u, 0u, 0u};
-            if (p.accumulate && r < p.R && c < p.N) {
-                const int pr = remap(r, p.skip0, p.skipw), pc = remap(c, p.skip0, p.skipw);
-                const E *src = C + (int64_t)pr * p.ldc + pc;
-                if (sizeof(E) == 1) {
-                    uint32_t w0 = 0u, w1 = 0u;
-                    if (VEC && c + 8 <= p.N) {
-                        uint2 v = *reinterpret_cast<const uint2 *>(src);
-                        w0 = v.x; w1 = v.y;
-                    } else {
-                        for (int t = 0; t < 8; ++t)
-                            if (c + t < p.N) {
-                                uint32_t e = (uint32_t)src[t] << (8 * (t % 4));
-                                if (t < 4) w0 |= e; else w1 |= e;
-                            }
-                    }
-                    q[0] = u8x2_lo(w0); q[1] = u8x2_hi(w0); q[2] = u8x2_lo(w1); q[3] = u8x2_hi(w1);
-                } else {
-                    if (VEC && c + 8 <= p.N) {
-                        uint4 v = *reinterpret_cast<const uint4 *>(src);
-                        q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
-                    } else {
-                        for (int t = 0; t < 8; ++t)
-                            if (c + t < p.N)
-                                q[t / 2] |= (uint32_t)src[t] << (16 * (t % 2));
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                acc[i][g * 4 + u] = q[u];
-        }
-    }
-
-    // ---- staging of one BK-deep k-panel: global -> registers -> shared
+    // ---- operand staging: global -> registers -> shared
     uint4 ra[Cfg::A_CHUNKS], rb[Cfg::B_CHUNKS];
-    auto gload = [&](int k0) {
+    auto gload = [&](int row0, int col0, int k0) {
 #pragma unroll
         for (int u = 0; u < Cfg::A_CHUNKS; ++u) {
             const int ch = tid + u * THREADS;
             const int i = ch % BM, kc = ch / BM;
             const int r = row0 + i;
-            ra[u] = r < p.R ? load_chunk<E, VEC>(A, p.lda, remap(r, p.skip0, p.skipw), k0 + kc * CH,
+            ra[u] = r < p.R ? load_chunk<E, VEC>(A, p.lda, remap(r, p.rskip0, p.rskipw), k0 + kc * CH,
                                                  0x7fffffff, p.K)
                             : make_uint4(0u, 0u, 0u, 0u);
         }
@@ -166,12 +139,10 @@ antidist_mul_kernel(MulArgs p)
             const int ch = tid + u * THREADS;
             const int jc = ch % (BN / CH), kr = ch / (BN / CH);
             const int c = col0 + jc * CH;
-            const int pc = c < p.N ? remap(c, p.skip0, p.skipw) : 0;
-            // column bound checked on the logical index; the chunk never straddles the gap
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (c < p.N && k0 + kr < p.K) {
-                const int lim = p.N - c;   // valid elements in this chunk
-                v = load_chunk<E, VEC>(B, p.ldb, k0 + kr, pc, p.K, pc + lim);
+            if (c < p.N && k0 + kr < p.K) {   // the chunk never straddles an excluded range
+                const int pc = remap(c, p.cskip0, p.cskipw);
+                v = load_chunk<E, VEC>(B, p.ldb, k0 + kr, pc, p.K, pc + (p.N - c));
             }
             rb[u] = v;
         }
@@ -205,79 +176,144 @@ antidist_mul_kernel(MulArgs p)
             }
         }
     };
-
-    const int nkt = (p.K + BK - 1) / BK;
-    gload(0);
-    sstore(0);
-    __syncthreads();
-
-    for (int kt = 0; kt < nkt; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nkt)
-            gload((kt + 1) * BK);
-        const uint32_t *a0p = sA0 + buf * BK * BM + tr * 4;
-        const uint32_t *a1p = sA1 + buf * BK * BM + tr * 4;
-        const uint32_t *bp = sB + buf * BK * BN2 + tc * 4;
-#pragma unroll 4
-        for (int k = 0; k < BK; ++k) {
-            uint32_t a0[TM], a1[TM], b[NP];
-#pragma unroll
-            for (int g = 0; g < TM / 4; ++g) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(a0p + k * BM + g * 4 * TR);
-                a0[4 * g] = v.x; a0[4 * g + 1] = v.y; a0[4 * g + 2] = v.z; a0[4 * g + 3] = v.w;
-                if (KD::AW == 2) {
-                    const uint4 w = *reinterpret_cast<const uint4 *>(a1p + k * BM + g * 4 * TR);
-                    a1[4 * g] = w.x; a1[4 * g + 1] = w.y; a1[4 * g + 2] = w.z; a1[4 * g + 3] = w.w;
-                } else {
-                    a1[4 * g] = a1[4 * g + 1] = a1[4 * g + 2] = a1[4 * g + 3] = 0u;
+    // C tile -> sC (raw bytes), asynchronously when vector accesses are allowed
+    auto cprefetch = [&](int row0, int col0) {
+        for (int ch = tid; ch < BM * CROW; ch += THREADS) {
+            const int i = ch / CROW, cc = ch % CROW;
+            const int r = row0 + i, c = col0 + cc * CH;
+            uint4 *dst = sC + ch;
+            if (VEC) {
+                const bool full = r < p.R && c + CH <= p.N;
+                if (full) {
+                    const E *src = C + (int64_t)remap(r, p.rskip0, p.rskipw) * p.ldc + remap(c, p.cskip0, p.cskipw);
+                    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+                    continue;
                 }
             }
-#pragma unroll
-            for (int g = 0; g < NP / 4; ++g) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(bp + k * BN2 + g * 4 * TC);
-                b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (r < p.R && c < p.N) {
+                const int pr = remap(r, p.rskip0, p.rskipw), pc = remap(c, p.cskip0, p.cskipw);
+                v = load_chunk<E, false>(C, p.ldc, pr, pc, 0x7fffffff, pc + (p.N - c));
             }
+            *dst = v;
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    if (tile < tiles) {
+        const int row0 = (tile / tiles_n) * BM, col0 = (tile % tiles_n) * BN;
+        if (p.accumulate) cprefetch(row0, col0);
+        gload(row0, col0, 0);
+    }
+
+    for (; tile < tiles; tile = advance(tile)) {
+        const int row0 = (tile / tiles_n) * BM, col0 = (tile % tiles_n) * BN;
+        const int next = advance(tile);
+        const int nrow0 = (next / tiles_n) * BM, ncol0 = (next % tiles_n) * BN;
+
+        uint32_t acc[TM][NP];
+        if (p.accumulate) {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const int li = (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+#pragma unroll
+                for (int g = 0; g < NP / 4; ++g) {
+                    const int lc = g * (8 * TC) + tc * 8;           // 8 entries
+                    const uint32_t *row = reinterpret_cast<const uint32_t *>(sC + li * CROW);
+                    if (sizeof(E) == 1) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(row + lc / 4);
+                        acc[i][g * 4] = u8x2_lo(v.x); acc[i][g * 4 + 1] = u8x2_hi(v.x);
+                        acc[i][g * 4 + 2] = u8x2_lo(v.y); acc[i][g * 4 + 3] = u8x2_hi(v.y);
+                    } else {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(row + lc / 2);
+                        acc[i][g * 4] = v.x; acc[i][g * 4 + 1] = v.y; acc[i][g * 4 + 2] = v.z; acc[i][g * 4 + 3] = v.w;
+                    }
+                }
+            }
+            __syncthreads();                                   // sC is free again
+            if (next < tiles) cprefetch(nrow0, ncol0);           // lands during this tile's k-loop
+        } else {
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < NP; ++j)
-                    acc[i][j] = KD::op(acc[i][j], b[j], a0[i], a1[i]);
+                for (int j = 0; j < NP; ++j) acc[i][j] = 0u;
         }
-        if (kt + 1 < nkt)
-            sstore(buf ^ 1);
-        __syncthreads();
-    }
 
-    // ---- epilogue
+        sstore(0);
+        __syncthreads();
+        for (int kt = 0; kt < nkt; ++kt) {
+            const int buf = kt & 1;
+            if (kt + 1 < nkt)
+                gload(row0, col0, (kt + 1) * BK);
+            else if (next < tiles)
+                gload(nrow0, ncol0, 0);                        // next tile's first k-panel
+            const uint32_t *a0p = sA0 + buf * BK * BM + tr * 4;
+            const uint32_t *a1p = sA1 + buf * BK * BM + tr * 4;
+            const uint32_t *bp = sB + buf * BK * BN2 + tc * 4;
+#pragma unroll 4
+            for (int k = 0; k < BK; ++k) {
+                uint32_t a0[TM], a1[TM], b[NP];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
-        if (r >= p.R)
-            continue;
-        const int pr = remap(r, p.skip0, p.skipw);
-#pragma unroll
-        for (int g = 0; g < NP / 4; ++g) {
-            const int c = col0 + g * (8 * TC) + tc * 8;
-            if (c >= p.N)
-                continue;
-            E *dst = C + (int64_t)pr * p.ldc + remap(c, p.skip0, p.skipw);
-            const uint32_t *q = &acc[i][g * 4];
-            if (sizeof(E) == 1) {
-                const uint32_t w0 = pack_u8x4(q[0], q[1]), w1 = pack_u8x4(q[2], q[3]);
-                if (VEC && c + 8 <= p.N) {
-                    *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
-                } else {
-                    for (int t = 0; t < 8; ++t)
-                        if (c + t < p.N)
-                            dst[t] = (E)(((t < 4 ? w0 : w1) >> (8 * (t % 4))) & 0xFFu);
+                for (int g = 0; g < TM / 4; ++g) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(a0p + k * BM + g * 4 * TR);
+                    a0[4 * g] = v.x; a0[4 * g + 1] = v.y; a0[4 * g + 2] = v.z; a0[4 * g + 3] = v.w;
+                    if (KD::AW == 2) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(a1p + k * BM + g * 4 * TR);
+                        a1[4 * g] = w.x; a1[4 * g + 1] = w.y; a1[4 * g + 2] = w.z; a1[4 * g + 3] = w.w;
+                    } else {
+                        a1[4 * g] = a1[4 * g + 1] = a1[4 * g + 2] = a1[4 * g + 3] = 0u;
+                    }
                 }
-            } else {
-                if (VEC && c + 8 <= p.N) {
-                    *reinterpret_cast<uint4 *>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+#pragma unroll
+                for (int g = 0; g < NP / 4; ++g) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(bp + k * BN2 + g * 4 * TC);
+                    b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
+                }
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        acc[i][j] = KD::op(acc[i][j], b[j], a0[i], a1[i]);
+            }
+            if (kt + 1 < nkt)
+                sstore(buf ^ 1);
+            __syncthreads();
+        }
+
+        // ---- epilogue
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+            if (r >= p.R)
+                continue;
+            const int pr = remap(r, p.rskip0, p.rskipw);
+#pragma unroll
+            for (int g = 0; g < NP / 4; ++g) {
+                const int c = col0 + g * (8 * TC) + tc * 8;
+                if (c >= p.N)
+                    continue;
+                E *dst = C + (int64_t)pr * p.ldc + remap(c, p.cskip0, p.cskipw);
+                const uint32_t *q = &acc[i][g * 4];
+                if (sizeof(E) == 1) {
+                    const uint32_t w0 = pack_u8x4(q[0], q[1]), w1 = pack_u8x4(q[2], q[3]);
+                    if (VEC && c + 8 <= p.N) {
+                        *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
+                    } else {
+                        for (int t = 0; t < 8; ++t)
+                            if (c + t < p.N)
+                                dst[t] = (E)(((t < 4 ? w0 : w1) >> (8 * (t % 4))) & 0xFFu);
+                    }
                 } else {
-                    for (int t = 0; t < 8; ++t)
-                        if (c + t < p.N)
-                            dst[t] = (E)((q[t / 2] >> (16 * (t % 2))) & 0xFFFFu);
+                    if (VEC && c + 8 <= p.N) {
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+                    } else {
+                        for (int t = 0; t < 8; ++t)
+                            if (c + t < p.N)
+                                dst[t] = (E)((q[t / 2] >> (16 * (t % 2))) & 0xFFFFu);
+                    }
                 }
             }
         }
@@ -285,28 +321,33 @@ antidist_mul_kernel(MulArgs p)
 }
 
 // -------------------------------------------------------------------------
-// Fused phases 1 + 2 of the blocked closure
+// Phase 1 of the blocked closure: close one pivot block in registers
 // -------------------------------------------------------------------------
-// 256 threads; thread (r0, c0), r0, c0 in [0,16), owns rows r0 + 16 j (j < TRN)
-// and lane-pair columns c0 + 16 m (m < TCN) of a PB×PB block, so pivot kk =
-// 16 j + q lives in register row j of threads r0 == q, and in register column
+// One CTA of 256 threads.  Thread (r0, c0), r0, c0 in [0,16), owns rows r0 + 16 j
+// (j < TRN) and lane-pair columns c0 + 16 m (m < TCN) of the PB×PB block, so pivot
+// kk = 16 j + q lives in register row j of threads r0 == q, and in register column
 // m = j/2, half q&1, of threads c0 == 8 (j&1) + q/2: every register index is a
-// compile-time constant while the pivot loop over q stays rolled.
+// compile-time constant while the pivot loop over q stays rolled.  Pivot rows and
+// columns are exchanged through double-buffered shared rows, one barrier per pivot.
+//
+// With kprev >= 0 the block first receives its phase-3 update from the previous
+// pivot block (T_kk ⊕= T_k,prev ⊗ T_prev,k), so that update can run here, off the
+// critical path of the main stream.
 template <class KD, int PB>
-struct PanelCfg {
+struct PivotCfg {
     static constexpr int TRN = PB / 16, TCN = PB / 32;
     static constexpr size_t SMEM = (size_t)KD::AW * PB * PB * 4   // sAt: [PB][PB] broadcast words
                                    + (size_t)PB * (PB / 2) * 4    // sBp: [PB][PB/2] lane pairs
                                    + 2 * (PB / 2) * 4             // rowbuf[2][PB/2]
                                    + 2 * PB * 2;                  // colbuf[2][PB] (u16)
-    static_assert(PB % 32 == 0 && PB >= 32, "panel");
+    static_assert(PB % 32 == 0 && PB >= 32, "pivot block");
 };
 
 template <class KD, int PB>
-__global__ void __launch_bounds__(256) antidist_panel_kernel(void *Tv, int64_t ldt, int D, int kb)
+__global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t ldt, int D, int kb, int kprev)
 {
     using E = typename KD::elem;
-    using Cfg = PanelCfg<KD, PB>;
+    using Cfg = PivotCfg<KD, PB>;
     constexpr int TRN = Cfg::TRN, TCN = Cfg::TCN;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sAt0 = smem;                                  // [PB][PB]: row kk, slot r0*TRN + j
@@ -318,20 +359,7 @@ __global__ void __launch_bounds__(256) antidist_panel_kernel(void *Tv, int64_t l
     E *T = static_cast<E *>(Tv);
     const int tid = threadIdx.x;
     const int r0 = tid >> 4, c0 = tid & 15;
-    const int nb = (D + PB - 1) / PB;
     const int k0 = kb * PB, bw = min(PB, D - k0);
-
-    // which block this CTA updates besides the diagonal one
-    int role = 0, bi = kb, bj = kb;               // 0: diagonal, 1: row panel, 2: column panel
-    if (blockIdx.x >= 1 && blockIdx.x < (unsigned)nb) {
-        role = 1;
-        bj = (int)blockIdx.x - 1;
-        if (bj >= kb) ++bj;
-    } else if (blockIdx.x >= (unsigned)nb) {
-        role = 2;
-        bi = (int)blockIdx.x - nb;
-        if (bi >= kb) ++bi;
-    }
 
     auto load_block = [&](int i0, int j0, int h, int w, uint32_t (&R)[TRN][TCN]) {
 #pragma unroll
@@ -348,21 +376,15 @@ __global__ void __launch_bounds__(256) antidist_panel_kernel(void *Tv, int64_t l
                 R[j][m] = v;
             }
     };
-    auto store_block = [&](int i0, int j0, int h, int w, const uint32_t (&R)[TRN][TCN]) {
-#pragma unroll
-        for (int j = 0; j < TRN; ++j)
-#pragma unroll
-            for (int m = 0; m < TCN; ++m) {
-                const int r = r0 + 16 * j, c = 2 * (c0 + 16 * m);
-                if (r < h) {
-                    E *dst = T + (int64_t)(i0 + r) * ldt + j0 + c;
-                    if (c < w) dst[0] = (E)(R[j][m] & 0xFFFFu);
-                    if (c + 1 < w) dst[1] = (E)(R[j][m] >> 16);
-                }
-            }
-    };
-    // A operand (entry (row, kk) broadcast) and B operand (row kk lane pairs)
-    auto store_Aform = [&](const uint32_t (&R)[TRN][TCN]) {
+
+    uint32_t X[TRN][TCN];
+    load_block(k0, k0, bw, bw, X);
+
+    if (kprev >= 0) {
+        // X ⊕= T[block kb rows][block kprev cols] ⊗ T[block kprev rows][block kb cols]
+        const int p0 = kprev * PB, pw = min(PB, D - p0);
+        uint32_t Y[TRN][TCN];
+        load_block(k0, p0, bw, pw, Y);                      // A operand, broadcast by column
 #pragma unroll
         for (int j = 0; j < TRN; ++j)
 #pragma unroll
@@ -370,24 +392,35 @@ __global__ void __launch_bounds__(256) antidist_panel_kernel(void *Tv, int64_t l
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     uint32_t a0, a1;
-                    KD::bcast((R[j][m] >> (16 * h)) & 0xFFFFu, a0, a1);
+                    KD::bcast((Y[j][m] >> (16 * h)) & 0xFFFFu, a0, a1);
                     const int kk = 2 * (c0 + 16 * m) + h;
                     sAt0[kk * PB + r0 * TRN + j] = a0;
                     if (KD::AW == 2) sAt1[kk * PB + r0 * TRN + j] = a1;
                 }
-    };
-    auto store_Bform = [&](const uint32_t (&R)[TRN][TCN]) {
+        load_block(p0, k0, pw, bw, Y);                      // B operand, lane pairs by row
 #pragma unroll
         for (int j = 0; j < TRN; ++j)
 #pragma unroll
             for (int m = 0; m < TCN; ++m)
-                sBp[(r0 + 16 * j) * (PB / 2) + c0 * TCN + m] = R[j][m];
-    };
+                sBp[(r0 + 16 * j) * (PB / 2) + c0 * TCN + m] = Y[j][m];
+        __syncthreads();
+        for (int kk = 0; kk < pw; ++kk) {
+            uint32_t bv[TCN], a0[TRN], a1[TRN];
+#pragma unroll
+            for (int m = 0; m < TCN; ++m) bv[m] = sBp[kk * (PB / 2) + c0 * TCN + m];
+#pragma unroll
+            for (int j = 0; j < TRN; ++j) {
+                a0[j] = sAt0[kk * PB + r0 * TRN + j];
+                a1[j] = KD::AW == 2 ? sAt1[kk * PB + r0 * TRN + j] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < TRN; ++j)
+#pragma unroll
+                for (int m = 0; m < TCN; ++m) X[j][m] = KD::op(X[j][m], bv[m], a0[j], a1[j]);
+        }
+    }
 
-    // ---------------- phase 1: close the diagonal block in registers
-    uint32_t X[TRN][TCN];
-    load_block(k0, k0, bw, bw, X);
-
+    // close the block: pivots kk = 0 .. bw-1
 #pragma unroll
     for (int j = 0; j < TRN; ++j) {
         for (int q = 0; q < 16; ++q) {
@@ -422,116 +455,221 @@ __global__ void __launch_bounds__(256) antidist_panel_kernel(void *Tv, int64_t l
         }
     }
 
-    if (role == 0) {
-        store_block(k0, k0, bw, bw, X);
-        return;
-    }
-
-    // ---------------- phase 2: one panel block, Y := Y ⊕ T_kk ⊗ Y or Y ⊕ Y ⊗ T_kk
-    const int i0 = bi * PB, j0 = bj * PB;
-    const int h = min(PB, D - i0), w = min(PB, D - j0);
-    uint32_t Y[TRN][TCN];
-    load_block(i0, j0, h, w, Y);
-    if (role == 1) {          // row panel: A = T_kk (closed), B = old Y
-        store_Aform(X);
-        store_Bform(Y);
-    } else {                  // column panel: A = old Y, B = T_kk (closed)
-        store_Aform(Y);
-        store_Bform(X);
-    }
-    __syncthreads();
-    for (int kk = 0; kk < bw; ++kk) {
-        uint32_t bv[TCN], a0[TRN], a1[TRN];
 #pragma unroll
-        for (int m = 0; m < TCN; ++m)
-            bv[m] = sBp[kk * (PB / 2) + c0 * TCN + m];
+    for (int j = 0; j < TRN; ++j)
 #pragma unroll
-        for (int j = 0; j < TRN; ++j) {
-            a0[j] = sAt0[kk * PB + r0 * TRN + j];
-            a1[j] = KD::AW == 2 ? sAt1[kk * PB + r0 * TRN + j] : 0u;
+        for (int m = 0; m < TCN; ++m) {
+            const int r = r0 + 16 * j, c = 2 * (c0 + 16 * m);
+            if (r < bw) {
+                E *dst = T + (int64_t)(k0 + r) * ldt + k0 + c;
+                if (c < bw) dst[0] = (E)(X[j][m] & 0xFFFFu);
+                if (c + 1 < bw) dst[1] = (E)(X[j][m] >> 16);
+            }
         }
-#pragma unroll
-        for (int j = 0; j < TRN; ++j)
-#pragma unroll
-            for (int m = 0; m < TCN; ++m)
-                Y[j][m] = KD::op(Y[j][m], bv[m], a0[j], a1[j]);
-    }
-    store_block(i0, j0, h, w, Y);
 }
 
 // -------------------------------------------------------------------------
 // Host launchers
 // -------------------------------------------------------------------------
 template <class KD, int BM, int BN, int BK, int TM, int TN>
-static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s)
+static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int reserve_sms = 0)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
-    dim3 grid((a.N + BN - 1) / BN, (a.R + BM - 1) / BM);
-    if (grid.y > 65535u)
-        return fail(SR_EINVAL, "antidist_mul: R too large for the tile grid (%d)", a.R);
+    const int64_t tiles = (int64_t)((a.N + BN - 1) / BN) * ((a.R + BM - 1) / BM);
+    if (tiles > 0x7fffffffLL)
+        return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
     auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
                     : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
-    static bool attr_set[2][kMaxDevices] = {};
+    static int occ[2][kMaxDevices] = {};
     const int dev = current_device();
-    if (!attr_set[vec][dev]) {
+    if (!occ[vec][dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-        attr_set[vec][dev] = true;
+        int n = 0;
+        SR_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Cfg::THREADS, Cfg::SMEM));
+        occ[vec][dev] = n > 0 ? n : 1;
     }
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+    int64_t grid = tiles;
+    if (reserve_sms > 0) {   // persistent: leave reserve_sms SMs free for concurrent work
+        const int64_t slots = (int64_t)std::max(1, device_sm_count() - reserve_sms) * occ[vec][dev];
+        grid = std::min(tiles, slots);
+    }
+    kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
 }
 
-sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s)
+sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles)
 {
     if (a.R <= 0 || a.N <= 0)
         return SR_OK;
+    if (tiles == 1)
+        return dt == SR_U8 ? launch_mul_cfg<KindU8, 64, 64, 32, 4, 8>(a, vec, s)
+                           : launch_mul_cfg<KindU16, 64, 64, 32, 4, 8>(a, vec, s);
+    const int reserve = 0;   // hardware block scheduling balances uneven tile counts best
     if (dt == SR_U8)
-        return launch_mul_cfg<KindU8, 128, 128, 32, 8, 16>(a, vec, s);
-    return launch_mul_cfg<KindU16, 128, 128, 32, 8, 16>(a, vec, s);
+        return launch_mul_cfg<KindU8, 128, 128, 32, 8, 16>(a, vec, s, reserve);
+    return launch_mul_cfg<KindU16, 128, 128, 32, 8, 16>(a, vec, s, reserve);
 }
 
 template <class KD, int PB>
-static sr_status launch_panel(void *T, int64_t ldt, int D, int kb, cudaStream_t s)
+static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cudaStream_t s)
 {
-    using Cfg = PanelCfg<KD, PB>;
-    const int nb = (D + PB - 1) / PB;
+    using Cfg = PivotCfg<KD, PB>;
     static bool attr[kMaxDevices] = {};
     const int dev = current_device();
     if (!attr[dev]) {
-        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_panel_kernel<KD, PB>,
+        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_pivot_kernel<KD, PB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
         attr[dev] = true;
     }
-    antidist_panel_kernel<KD, PB><<<2 * nb - 1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb);
+    antidist_pivot_kernel<KD, PB><<<1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb, kprev);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
 }
 
+// Side stream (high priority) and a per-thread pool of events for the look-ahead.
+static cudaStream_t side_stream()
+{
+    static cudaStream_t st[kMaxDevices] = {};
+    static std::mutex mu;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev]) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&st[dev], cudaStreamNonBlocking, hi) != cudaSuccess)
+            st[dev] = nullptr;
+    }
+    return st[dev];
+}
+
+static sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
+{
+    static thread_local std::vector<cudaEvent_t> pool[kMaxDevices];
+    std::vector<cudaEvent_t> &p = pool[current_device()];
+    while (p.size() < n) {
+        cudaEvent_t e;
+        SR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p.push_back(e);
+    }
+    out = &p;
+    return SR_OK;
+}
+
+// Phase 3 of pivot block kb restricted to a set of blocks: rows [r0, r0+nr) and
+// columns [c0, c0+nc) of the matrix, each with one excluded range.
+template <class KD>
+static sr_status phase3(void *T, int64_t ldt, int k0, int bw, int rbeg, int R, int rskip0, int rskipw, int cbeg,
+                        int N, int cskip0, int cskipw, sr_dtype dt, bool vec, cudaStream_t s, int tiles,
+                        int skip_tile = -1)
+{
+    using E = typename KD::elem;
+    E *Te = static_cast<E *>(T);
+    MulArgs a;
+    a.A = Te + (int64_t)rbeg * ldt + k0;                 // column panel: rows from rbeg, columns of block k
+    a.B = Te + (int64_t)k0 * ldt + cbeg;                 // row panel: rows of block k, columns from cbeg
+    a.C = Te + (int64_t)rbeg * ldt + cbeg;
+    a.lda = a.ldb = a.ldc = ldt;
+    a.R = R;
+    a.N = N;
+    a.K = bw;
+    a.accumulate = 1;
+    a.rskip0 = rskip0; a.rskipw = rskipw;
+    a.cskip0 = cskip0; a.cskipw = cskipw;
+    a.skip_tile = skip_tile;
+    return launch_antidist_mul(a, dt, vec, s, tiles);
+}
+
+// Phase 2 of pivot block kb as two in-place products on many CTAs:
+//   row panel    T_kj := T_kj ⊕ T_kk ⊗ T_kj   (B and C are the same panel)
+//   column panel T_ik := T_ik ⊕ T_ik ⊗ T_kk   (A and C are the same panel)
+// with T_kk already closed.  A CTA may read panel entries another CTA has already
+// updated; that is harmless: for any T_kj <= X <= T_kj ⊕ T_kk ⊗ T_kj entrywise,
+// T_kj ⊕ T_kk ⊗ X = T_kj ⊕ T_kk ⊗ T_kj, because T_kk ⊗ T_kk <= T_kk (closed) and
+// ⊗ distributes over ⊕ and is monotone.  Each entry read is either its old or its
+// new value (byte / 16-bit entries are never torn).
+template <class KD>
+static sr_status phase2(void *T, int64_t ldt, int D, int k0, int bw, bool row, sr_dtype dt, bool vec,
+                        cudaStream_t s)
+{
+    using E = typename KD::elem;
+    E *Te = static_cast<E *>(T);
+    if (D - bw <= 0)
+        return SR_OK;
+    MulArgs a;
+    a.lda = a.ldb = a.ldc = ldt;
+    a.K = bw;
+    a.accumulate = 1;
+    a.skip_tile = -1;
+    if (row) {      // rows of block k, all columns but block k
+        a.A = Te + (int64_t)k0 * ldt + k0;
+        a.B = Te + (int64_t)k0 * ldt;
+        a.C = Te + (int64_t)k0 * ldt;
+        a.R = bw; a.N = D - bw;
+        a.rskip0 = 0x7fffffff; a.rskipw = 0;
+        a.cskip0 = k0; a.cskipw = bw;
+    } else {        // all rows but block k, columns of block k
+        a.A = Te + k0;
+        a.B = Te + (int64_t)k0 * ldt + k0;
+        a.C = Te + k0;
+        a.R = D - bw; a.N = bw;
+        a.rskip0 = k0; a.rskipw = bw;
+        a.cskip0 = 0x7fffffff; a.cskipw = 0;
+    }
+    return launch_antidist_mul(a, dt, vec, s, 1);
+}
+
+// Pipelined three-phase blocked closure (pivot blocks of PB = 128), two streams:
+//   main  : phase 2 row panel of kb | phase 3 of kb (all blocks outside block row and
+//           column kb except the diagonal block kb+1; persistent grid leaving one SM)
+//   side  : phase 2 column panel of kb | block (kb+1, kb+1): its phase-3 update
+//           from pivot kb, then its closure (phase 1 of kb+1), on one CTA
+// so the two panel products run side by side and the serial pivot chain overlaps
+// the bulk of phase 3.  The side stream's pivot CTA reads only panel kb (final once
+// both phase-2 products are done) and writes only the diagonal block, which the
+// concurrent phase 3 skips.
 template <class KD>
 static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s)
 {
-    constexpr int PB = 64;
+    constexpr int PB = 128;
     const int nb = (D + PB - 1) / PB;
-    using E = typename KD::elem;
+    SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, s)));
+    if (nb == 1)
+        return SR_OK;
+    cudaStream_t s2 = side_stream();
+    std::vector<cudaEvent_t> *ev = nullptr;
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
     for (int kb = 0; kb < nb; ++kb) {
         const int k0 = kb * PB, bw = std::min(PB, D - k0);
-        SR_TRY((launch_panel<KD, PB>(T, ldt, D, kb, s)));
-        if (nb > 1) {
-            MulArgs a;
-            a.A = static_cast<const E *>(T) + k0;
-            a.B = static_cast<const E *>(T) + (int64_t)k0 * ldt;
-            a.C = T;
-            a.lda = a.ldb = a.ldc = ldt;
-            a.R = a.N = D - bw;
-            a.K = bw;
-            a.accumulate = 1;
-            a.skip0 = k0;
-            a.skipw = bw;
-            SR_TRY(launch_antidist_mul(a, dt, vec, s));
+        const bool next = kb + 1 < nb;
+        if (!s2) {   // single stream: phase 2, phase 3, next pivot
+            SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
+            SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s));
+            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
+            if (next) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, s)));
+            continue;
         }
+        cudaEvent_t *e = ev->data() + 4 * kb;
+        SR_CUDA_CHECK(cudaEventRecord(e[0], s));                 // pivot kb closed (main order)
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
+        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s2));
+        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
+        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));          // both panels done
+        if (!next) {
+            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
+            break;
+        }
+        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
+        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, s2)));
+        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
+        // block (kb+1, kb+1) is logical tile (kb, kb) once block row/column kb are removed
+        const int tiles_n = (D - bw + PB - 1) / PB;
+        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 2, kb * tiles_n + kb));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
     }
     return SR_OK;
 }

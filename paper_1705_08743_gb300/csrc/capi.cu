@@ -272,7 +272,9 @@ sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int6
     a.lda = lda; a.ldb = ldb; a.ldc = ldc;
     a.R = (int)R; a.K = (int)K; a.N = (int)N;
     a.accumulate = accumulate ? 1 : 0;
-    a.skip0 = 0x7fffffff; a.skipw = 0;
+    a.rskip0 = a.cskip0 = 0x7fffffff;
+    a.rskipw = a.cskipw = 0;
+    a.skip_tile = -1;
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
     return launch_antidist_mul(a, dtype, vec, S(stream));
 }

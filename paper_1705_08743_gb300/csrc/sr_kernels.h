@@ -14,8 +14,8 @@ int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
-// and columns of B/C with logical index >= skip0 are shifted by skipw (the
-// closure's phase 3 excludes the pivot block's rows and columns this way).
+// with logical index >= rskip0 are shifted by rskipw, columns of B/C with logical
+// index >= cskip0 by cskipw (the closure's phase 3 excludes pivot blocks this way).
 struct MulArgs {
     const void *A;
     const void *B;
@@ -23,10 +23,14 @@ struct MulArgs {
     int64_t lda, ldb, ldc;     // elements (anti-distance) or 32-bit words (Boolean)
     int R, K, N;               // logical sizes: anti-distance entries / Boolean bits
     int accumulate;
-    int skip0, skipw;
+    int rskip0, rskipw;
+    int cskip0, cskipw;
+    int skip_tile = -1;        // a tile (row-major index, 128x128 tiles) left untouched, or -1
 };
 
-sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s);
+// tiles: 0 = 128x128 CTA tiles (throughput), 1 = 64x64 (latency: more CTAs for small grids),
+//        2 = 128x128 on a persistent grid that leaves one SM free for concurrent work
+sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
 sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s);
 sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ldt, int R, int C,
                                  sr_dtype dt, int num_sms, cudaStream_t s);

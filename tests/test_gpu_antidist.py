@@ -96,6 +96,18 @@ def test_closure_random(dt, D):
 
 
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("D", [256, 257, 385, 640, 1100])
+def test_closure_many_pivot_blocks(dt, D):
+    """Several 128-wide pivot blocks: exercises the look-ahead (next pivot's panels
+    on a second stream while the rest of phase 3 runs) and ragged last blocks."""
+    rng = np.random.default_rng(D + 7)
+    S = S_OF[dt]
+    for dens, lo in [(2.0 / D, S - S // 10), (0.05, 1)]:
+        A = rand_anti(rng, D, D, dt, dens, lo)
+        assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 def test_closure_unaligned_ld(dt):
     rng = np.random.default_rng(8)
     A = rand_anti(rng, 150, 150, dt, 0.05, S_OF[dt] - 40)
