@@ -530,7 +530,7 @@ static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cu
 }
 
 // Side stream (high priority) and a per-thread pool of events for the look-ahead.
-static cudaStream_t side_stream()
+cudaStream_t side_stream()
 {
     static cudaStream_t st[kMaxDevices] = {};
     static std::mutex mu;
@@ -545,7 +545,7 @@ static cudaStream_t side_stream()
     return st[dev];
 }
 
-static sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
+sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
 {
     static thread_local std::vector<cudaEvent_t> pool[kMaxDevices];
     std::vector<cudaEvent_t> &p = pool[current_device()];

@@ -181,7 +181,7 @@ bool_mul_kernel(BoolArgs p)
 #pragma unroll
         for (int u = 0; u < TNW; ++u) {
             const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
-            if (w < p.ncw) {
+            if (w < p.ncw && !(r >= p.kr0 && r < p.kr0 + p.krn && w >= p.kw0 && w < p.kw0 + p.kwn)) {
                 const int pw = bremap(w, p.skip0w, p.skipww);
                 dst[pw] = acc[i][u] & word_mask(pw, p.N);
             }
@@ -355,13 +355,92 @@ static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
     return SR_OK;
 }
 
-sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s)
+sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape)
 {
     if (a.R <= 0 || a.ncw <= 0)
         return SR_OK;
+    if (shape == 1)          // panels a few words wide: 128 rows x 4 words per CTA
+        return launch_bool_cfg<128, 4, 4, 4, 4>(a, vec, s);
+    if (shape == 2)          // panels a few rows high: 32 rows x 16 words per CTA
+        return launch_bool_cfg<32, 16, 4, 4, 4>(a, vec, s);
     return launch_bool_cfg<128, 64, 4, 4, 16>(a, vec, s);
 }
 
+// Phase 1 of the pipelined Boolean closure: one CTA, one thread per row of the
+// PB-bit pivot block.  With kprev >= 0 the block first receives its phase-3
+// update from the previous pivot block: X := X ⊕ T[k rows][prev cols] ⊗ T[prev rows][k cols].
+template <int PB>
+__global__ void __launch_bounds__(PB) bool_pivot_kernel(uint32_t *T, int64_t ldt, int D, int rw, int kb, int kprev)
+{
+    constexpr int PW = PB / 32;
+    __shared__ __align__(16) uint32_t sB[PB][PW];
+    __shared__ __align__(16) uint32_t rowbuf[2][PW];
+    const int i = threadIdx.x;
+    const int k0 = kb * PB, bw = min(PB, D - k0), kw0 = k0 / 32;
+    uint32_t X[PW];
+#pragma unroll
+    for (int u = 0; u < PW; ++u)
+        X[u] = (i < bw && kw0 + u < rw) ? T[(int64_t)(k0 + i) * ldt + kw0 + u] & word_mask(kw0 + u, D) : 0u;
+    if (kprev >= 0) {
+        const int p0 = kprev * PB, pw0 = p0 / 32;       // the previous block is a full block
+        uint32_t Arow[PW];
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            Arow[u] = i < bw ? T[(int64_t)(k0 + i) * ldt + pw0 + u] : 0u;
+            sB[i][u] = kw0 + u < rw ? T[(int64_t)(p0 + i) * ldt + kw0 + u] & word_mask(kw0 + u, D) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < PW; ++w)
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t m = (uint32_t)((int32_t)(Arow[w] << (31 - b)) >> 31);
+#pragma unroll
+                for (int u = 0; u < PW; ++u) X[u] |= sB[32 * w + b][u] & m;
+            }
+    }
+#pragma unroll
+    for (int w = 0; w < PW; ++w) {
+        for (int b = 0; b < 32; ++b) {
+            const int kk = 32 * w + b;
+            if (kk >= bw) break;
+            const int par = kk & 1;
+            if (i == kk) {
+#pragma unroll
+                for (int u = 0; u < PW; ++u) rowbuf[par][u] = X[u];
+            }
+            __syncthreads();
+            const uint32_t m = (uint32_t)((int32_t)(X[w] << (31 - b)) >> 31);
+#pragma unroll
+            for (int u = 0; u < PW; ++u) X[u] |= rowbuf[par][u] & m;
+        }
+    }
+    if (i < bw) {
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if (kw0 + u < rw)
+                T[(int64_t)(k0 + i) * ldt + kw0 + u] = X[u] & word_mask(kw0 + u, D);
+    }
+}
+
+static BoolArgs bool_args(const uint32_t *A, const uint32_t *B, uint32_t *C, int64_t ld, int R, int K, int N, int ncw)
+{
+    BoolArgs a;
+    a.A = A; a.B = B; a.C = C;
+    a.lda = a.ldb = a.ldc = ld;
+    a.R = R; a.K = K; a.N = N;
+    a.ncw = ncw;
+    a.accumulate = 1;
+    a.skip0 = 0x7fffffff; a.skipw = 0;
+    a.skip0w = 0x7fffffff; a.skipww = 0;
+    return a;
+}
+
+// Pipelined blocked Warshall on bit rows (the same schedule as the anti-distance
+// closure): per pivot block kb, phase 2 as two in-place products (row panel on the
+// main stream, column panel on a high-priority side stream; monotone OR updates make
+// the in-place read/write overlap harmless), then phase 3 on the main stream over all
+// rows and words outside block kb, leaving the next diagonal block unwritten, while
+// one CTA on the side stream gives that block its update from pivot kb and closes it.
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
 {
     constexpr int PB = 128, PW = PB / 32;
@@ -369,34 +448,64 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
     bool_clear_pad_kernel<<<(D + 255) / 256, 256, 0, s>>>(T, ldt, D, D, rw);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
-    for (int kb = 0; kb < nb; ++kb) {
-        const int k0 = kb * PB, bw = std::min(PB, D - k0);
-        bool_panel_kernel<PB><<<2 * nb - 1, PB, 0, s>>>(T, ldt, D, rw, kb);
+    auto pivot = [&](int kb, int kprev, cudaStream_t st) -> sr_status {
+        bool_pivot_kernel<PB><<<1, PB, 0, st>>>(T, ldt, D, rw, kb, kprev);
         SR_CUDA_CHECK(cudaGetLastError());
-    count_launches();
-        if (nb > 1) {
-            BoolArgs a;
-            a.A = T + k0 / 32;
-            a.B = T + (int64_t)k0 * ldt;
-            a.C = T;
-            a.lda = a.ldb = a.ldc = ldt;
-            a.R = D - bw;
-            a.K = bw;
-            a.N = D;
-            a.accumulate = 1;
-            a.skip0 = k0;
-            a.skipw = bw;
-            if (kb + 1 < nb) {
-                a.ncw = rw - PW;
-                a.skip0w = k0 / 32;
-                a.skipww = PW;
-            } else {
-                a.ncw = k0 / 32;
-                a.skip0w = a.ncw;
-                a.skipww = 0;
-            }
-            SR_TRY(launch_bool_mul(a, vec, s));
+        count_launches();
+        return SR_OK;
+    };
+    SR_TRY(pivot(0, -1, s));
+    if (nb == 1)
+        return SR_OK;
+    cudaStream_t s2 = side_stream();
+    std::vector<cudaEvent_t> *ev = nullptr;
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * PB, bw = std::min(PB, D - k0), kw = k0 / 32;
+        const int bwords = (bw + 31) / 32;
+        const bool next = kb + 1 < nb;
+        // phase 2: row panel (rows of block kb, all words but its own) ...
+        BoolArgs rowp = bool_args(T + (int64_t)k0 * ldt + kw, T + (int64_t)k0 * ldt, T + (int64_t)k0 * ldt, ldt,
+                                  bw, bw, D, next ? rw - PW : kw);
+        rowp.skip0w = next ? kw : 0x7fffffff;
+        rowp.skipww = next ? PW : 0;
+        // ... and column panel (all rows but block kb, the words of block kb)
+        BoolArgs colp = bool_args(T + kw, T + (int64_t)k0 * ldt + kw, T + kw, ldt, D - bw, bw, bw, bwords);
+        colp.skip0 = k0;
+        colp.skipw = bw;
+        // phase 3: all rows but block kb, all words but those of block kb
+        BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D - bw, bw, D, next ? rw - PW : kw);
+        p3.skip0 = k0;
+        p3.skipw = bw;
+        p3.skip0w = next ? kw : 0x7fffffff;
+        p3.skipww = next ? PW : 0;
+        if (!s2) {
+            SR_TRY(launch_bool_mul(rowp, vec, s, 2));
+            SR_TRY(launch_bool_mul(colp, vec, s, 1));
+            SR_TRY(launch_bool_mul(p3, vec, s));
+            if (next) SR_TRY(pivot(kb + 1, -1, s));
+            continue;
         }
+        cudaEvent_t *e = ev->data() + 4 * kb;
+        SR_CUDA_CHECK(cudaEventRecord(e[0], s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
+        SR_TRY(launch_bool_mul(colp, vec, s2, 1));
+        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
+        SR_TRY(launch_bool_mul(rowp, vec, s, 2));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));
+        if (!next) {
+            SR_TRY(launch_bool_mul(p3, vec, s));
+            break;
+        }
+        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
+        SR_TRY(pivot(kb + 1, kb, s2));
+        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
+        // block (kb+1, kb+1) sits at logical rows [k0, k0+PB), logical words [kw, kw+PW)
+        p3.kr0 = k0; p3.krn = PB;
+        p3.kw0 = kw; p3.kwn = PW;
+        SR_TRY(launch_bool_mul(p3, vec, s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
     }
     return SR_OK;
 }

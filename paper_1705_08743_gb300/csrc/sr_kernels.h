@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/semiring.h"
 
 namespace sr {
@@ -12,6 +14,8 @@ constexpr int kMaxDevices = 64;
 int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
+cudaStream_t side_stream();    // per-device high-priority stream for look-ahead work (may be null)
+sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
 // with logical index >= rskip0 are shifted by rskipw, columns of B/C with logical
@@ -47,8 +51,11 @@ struct BoolArgs {
     int accumulate;
     int skip0, skipw;          // excluded row range (rows of A and C)
     int skip0w, skipww;        // excluded word range (words of B and C)
+    int kr0 = -1, krn = 0;     // a block of C left unwritten: logical rows [kr0, kr0+krn) ...
+    int kw0 = 0, kwn = 0;      // ... and logical words [kw0, kw0+kwn) (kr0 = -1: none)
 };
-sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s);
+// shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
+sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape = 0);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
                            int rw, int num_sms, cudaStream_t s);

@@ -109,7 +109,7 @@ def sq_ctx():
 
 
 @pytest.mark.parametrize("w", [32, 64])
-@pytest.mark.parametrize("D", [1, 5, 31, 32, 33, 64, 65, 127, 128, 129, 200, 300, 513])
+@pytest.mark.parametrize("D", [1, 5, 31, 32, 33, 64, 65, 127, 128, 129, 130, 200, 256, 300, 385, 513, 700])
 def test_bool_closure(w, D, sq_ctx):
     import paper_1705_08743_gb300 as sr
     rng = np.random.default_rng(D * 3 + w)
