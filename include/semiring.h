@@ -96,6 +96,14 @@ const char *sr_version(void);
 /* Device workspace bytes a call would need (0 for calls that need none). */
 sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size_t *bytes);
 
+/* Options of a context. */
+typedef enum {
+    SR_OPT_BOOL_TENSOR = 1   /* Boolean products on the tensor cores (count, then test > 0):
+                                0 never, 1 when K >= 1024 (default), 2 whenever possible.
+                                Used only with enough ctx workspace (sr_workspace_query). */
+} sr_option;
+sr_status sr_set_option(sr_ctx *ctx, int option, int value);
+
 /* ---------------------------------------------------------------- encoding (Sections 3-4) */
 
 /* T (R×C, dtype SR_U8 or SR_U16) := anti-distance encoding of integer edge
@@ -124,7 +132,11 @@ sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, i
 
 /* Boolean product of bit matrices: C := (accumulate ? C : 0) ⊕ A ⊗ B,
  * (A ⊗ B)_ij = OR over k of (A_ik AND B_kj).  dtype SR_BOOL_W32 or W64;
- * lda/ldb/ldc in words.  C must not overlap A or B. */
+ * lda/ldb/ldc in words.  C must not overlap A or B.
+ * With a ctx whose workspace holds sr_workspace_query(SR_OP_BOOL_MUL, ..) bytes for
+ * max(R, K, N), the product runs on the tensor cores as a count (fp8 0/1 operands,
+ * fp32 sums, exact) followed by the test count > 0 (SR_OPT_BOOL_TENSOR); otherwise
+ * on 32-bit word AND/OR. */
 sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb,
                    void *C, int64_t ldc, int64_t R, int64_t K, int64_t N,
                    sr_dtype dtype, int accumulate, void *stream);

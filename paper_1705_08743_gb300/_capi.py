@@ -29,6 +29,7 @@ SR_BOOL_W32, SR_BOOL_W64, SR_U8, SR_U16 = range(4)
 SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
 SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
 SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD = range(4)
+SR_OPT_BOOL_TENSOR = 1
 
 STATUS_NAMES = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ETIMEOUT",
                 5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND"}
@@ -86,6 +87,7 @@ _SIGS = {
     "sr_workspace_query": (_st, [_int, _int, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "sr_stream_status": (_st, [_vp, _vp]),
     "sr_kernel_launches": (ctypes.c_uint64, []),
+    "sr_set_option": (_st, [_vp, _int, _int]),
     "sr_peak_probe": (_st, [_int, _int, _int, _vp, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "antidist_encode": (_st, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
@@ -180,6 +182,10 @@ def sr_workspace_query(op: int, dtype: int, D: int, method: int = 0) -> int:
 
 def sr_stream_status(ctx, stream=None):
     _check(lib.sr_stream_status(ctx, _stream(stream)), "sr_stream_status")
+
+
+def sr_set_option(ctx, option: int, value: int):
+    _check(lib.sr_set_option(ctx, option, value), "sr_set_option")
 
 
 def sr_kernel_launches() -> int:

@@ -1,0 +1,362 @@
+// Boolean product on the 5th-generation tensor cores: count, then test > 0.
+//
+// (A ⊗ B)_ij = OR_k (A_ik AND B_kj) equals [Σ_k A_ik·B_kj > 0] over the integers
+// (Section 2's ∨/∧ product read as a count).  A and B are expanded from bits to
+// fp8 e4m3 bytes (1.0 = 0x38, 0 = 0x00), multiplied by tcgen05.mma (kind::f8f6f4,
+// fp32 accumulation in tensor memory), and each fp32 count becomes one bit again.
+// Exact: every product is 0 or 1, every partial sum a non-negative integer, and
+// rounding a sum of non-negative numbers never reaches 0 from a positive value
+// (below 2^24, fp32 holds the counts exactly anyway).
+//
+// Kernel: one CTA per 128×256 output tile (M = 128, N = 256 per MMA, K = 32 per
+// MMA), 4 warps.  Warp 0 lane 0 streams 128-byte-deep K slices of A (128 rows) and
+// B^T (256 rows) with TMA into a 4-stage shared-memory ring (128-byte swizzle);
+// warp 1 lane 0 issues the MMAs and releases each stage with tcgen05.commit; then
+// all four warps read their 32 accumulator lanes from tensor memory (tcgen05.ld),
+// turn 32 counts into one 32-bit word and OR it into C.  Every wait on an
+// mbarrier is bounded; a wait that gives up sets a status word and the CTA stops
+// issuing work, waits (bounded) for the MMAs it started, frees its tensor memory
+// and returns.
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "sr_common.cuh"
+#include "sr_kernels.h"
+
+namespace sr {
+
+namespace tc {
+constexpr int BM = 128, BN = 256, BK = 128;          // BK in bytes = fp8 elements
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK;
+constexpr size_t SMEM = 1024 + (size_t)STAGES * (A_BYTES + B_BYTES) + 128;
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;     // tries per wait before giving up
+}  // namespace tc
+
+struct BoolTcArgs {
+    uint32_t *C;
+    int64_t ldc;          // 32-bit words
+    int R, N;             // rows of C; bits per row of C (pad bits written 0)
+    int ncw;              // 32-bit words per row of C to write
+    int nkb;              // K slices of BK bytes
+    int accumulate;
+    int *status;          // nonzero after a bounded wait gave up (may be null)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// true once the phase with the given parity has completed; false after SPIN_LIMIT tries
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < tc::SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+// shared-memory matrix descriptor: K-major tile with 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32"
+                 " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15,"
+                 " %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, BoolTcArgs p)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;                                              // [STAGES][BM][BK]
+    uint8_t *sB = smem + tc::STAGES * tc::A_BYTES;                   // [STAGES][BN][BK]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + tc::STAGES * tc::B_BYTES);  // full[S], empty[S], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * tc::STAGES + 1);
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = blockIdx.y * tc::BM, ncol0 = blockIdx.x * tc::BN;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES), done = smem_u32(bars + 2 * tc::STAGES);
+
+    if (tid == 0) {
+        failed = 0;
+        for (int s = 0; s < tc::STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(tmem_slot)), "r"(tc::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // instruction descriptor: f32 accumulate, A = B = e4m3, both K-major, N = 256, M = 128
+    const uint32_t idesc = (1u << 4) | ((uint32_t)(tc::BN >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
+    int nload = 0;    // K slices whose TMA loads warp 0 lane 0 issued
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < p.nkb; ++kb) {
+            const int s = kb % tc::STAGES;
+            if (kb >= tc::STAGES && !mbar_wait(empty0 + 8 * s, ((kb / tc::STAGES) - 1) & 1)) {
+                atomicExch(&failed, 1);
+                break;
+            }
+            if (*(volatile int *)&failed) break;
+            mbar_expect_tx(full0 + 8 * s, tc::A_BYTES + tc::B_BYTES);
+            tma_load_2d(smem_u32(sA + s * tc::A_BYTES), &tA, kb * tc::BK, row0, full0 + 8 * s);
+            tma_load_2d(smem_u32(sB + s * tc::B_BYTES), &tB, kb * tc::BK, ncol0, full0 + 8 * s);
+            ++nload;
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < p.nkb; ++kb) {
+            const int s = kb % tc::STAGES;
+            if (!mbar_wait(full0 + 8 * s, (kb / tc::STAGES) & 1)) {
+                atomicExch(&failed, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * tc::A_BYTES), b0 = smem_u32(sB + s * tc::B_BYTES);
+#pragma unroll
+            for (int k4 = 0; k4 < tc::BK / 32; ++k4)
+                umma_f8(tmem, smem_desc(a0 + 32 * k4), smem_desc(b0 + 32 * k4), idesc, (kb | k4) != 0);
+            umma_commit(empty0 + 8 * s);
+        }
+        umma_commit(done);          // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    // epilogue: 32 accumulator lanes per warp, 32 columns per tensor-memory load
+    const bool ok = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) atomicExch(&failed, 1);
+    __syncthreads();
+    const bool good = !failed;
+    const int r = row0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int c = 0; c < tc::BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);   // whole warp, converged
+        uint32_t word = 0u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) word |= (v[j] != 0u ? 1u : 0u) << j;
+        const int w = (ncol0 >> 5) + c;
+        if (good && r < p.R && w < p.ncw) {
+            const int lo = w * 32;
+            const uint32_t mask = lo + 32 <= p.N ? 0xFFFFFFFFu : (lo >= p.N ? 0u : (1u << (p.N - lo)) - 1u);
+            uint32_t *dst = p.C + (int64_t)r * p.ldc + w;
+            *dst = ((p.accumulate ? *dst : 0u) | word) & mask;
+        }
+    }
+    if (!good) {
+        if (tid == 0 && p.status) atomicExch(p.status, 1);
+        // drain: every TMA copy this CTA started must land before its shared memory is released
+        if (warp == 0 && lane == 0)
+            for (int s = 0; s < tc::STAGES && s < nload; ++s) {
+                const int loads = (nload - 1 - s) / tc::STAGES + 1;      // loads issued to stage s
+                mbar_wait(full0 + 8 * s, (loads - 1) & 1);
+            }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::TMEM_COLS)
+                     : "memory");
+}
+
+// bits -> e4m3 bytes (1.0 = 0x38), rows x Kp, zero past K
+__global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp)
+{
+    const int64_t total = (int64_t)rows * (Kp / 32);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / (Kp / 32)), w = (int)(t % (Kp / 32));
+        const int lo = 32 * w;
+        uint32_t bits = lo < K ? M[(int64_t)r * ldm + w] : 0u;
+        if (lo + 32 > K) bits &= lo >= K ? 0u : (1u << (K - lo)) - 1u;
+        uint32_t o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t nib = (bits >> (4 * q)) & 0xFu;
+            o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
+                   ((nib & 8u) ? 0x38000000u : 0u);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (int64_t)r * Kp + lo);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+// transpose + expand: out[n][k] = bit (k, n) of M (K rows of bits), rows n < N, zero past K
+__global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwords = (N + 31) / 32, kblocks = Kp / 32;
+    const int64_t total = (int64_t)nwords * kblocks;
+    const int64_t wid = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t t = wid; t < total; t += nw) {
+        const int w = (int)(t / kblocks), kb = (int)(t % kblocks);
+        const int k = 32 * kb + lane;
+        const uint32_t word = k < K ? M[(int64_t)k * ldm + w] : 0u;   // row k, columns 32w .. 32w+31
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, (word >> j) & 1u);   // column 32w + j, rows 32kb..+31
+            if (lane == j) mine = b;
+        }
+        const int n = 32 * w + lane;
+        if (n < N) {
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t nib = (mine >> (4 * q)) & 0xFu;
+                o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
+                       ((nib & 8u) ? 0x38000000u : 0u);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(out + (int64_t)n * Kp + 32 * kb);
+            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap *m, void *base, int rows, int Kp, int box_rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N)
+{
+    const int64_t Kp = (K + tc::BK - 1) / tc::BK * tc::BK;
+    return (size_t)((R + N) * Kp) + 1024;
+}
+
+bool bool_tc_available()
+{
+    int dev = current_device(), major = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+    return major == 10 && encode_fn() != nullptr;
+}
+
+sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s)
+{
+    const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
+    if (bool_tc_workspace(a.R, a.K, a.N) > ws_bytes)
+        return fail(SR_ENOMEM, "bool_mul (tensor path): workspace too small");
+    uint8_t *Ae = static_cast<uint8_t *>(ws);
+    uint8_t *Be = Ae + (int64_t)a.R * Kp;
+    Be = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(Be) + 255) & ~uintptr_t(255));
+    const int sms = device_sm_count();
+    {
+        const int64_t n = (int64_t)a.R * (Kp / 32);
+        expand_rows_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sms * 16)), 256, 0, s>>>(
+            a.A, a.lda, a.R, a.K, Ae, Kp);
+        SR_CUDA_CHECK(cudaGetLastError());
+        const int64_t nw = (int64_t)((a.N + 31) / 32) * (Kp / 32);
+        expand_cols_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((nw + 7) / 8, sms * 16)), 256, 0, s>>>(
+            a.B, a.ldb, a.K, a.N, Be, Kp);
+        SR_CUDA_CHECK(cudaGetLastError());
+        count_launches(2);
+    }
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, Ae, a.R, Kp, tc::BM) || !make_map(&mB, Be, a.N, Kp, tc::BN))
+        return fail(SR_ECUDA, "bool_mul (tensor path): cannot encode the tensor maps");
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(bool_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
+        attr[dev] = true;
+    }
+    BoolTcArgs p;
+    p.C = a.C;
+    p.ldc = a.ldc;
+    p.R = a.R;
+    p.N = a.N;
+    p.ncw = a.ncw;
+    p.nkb = Kp / tc::BK;
+    p.accumulate = a.accumulate;
+    p.status = status;
+    dim3 grid((a.ncw + tc::BN / 32 - 1) / (tc::BN / 32), (a.R + tc::BM - 1) / tc::BM);
+    bool_tc_kernel<<<grid, 128, tc::SMEM, s>>>(mA, mB, p);
+    SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
+    return SR_OK;
+}
+
+}  // namespace sr

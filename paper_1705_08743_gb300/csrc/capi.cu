@@ -181,6 +181,17 @@ void sr_destroy(sr_ctx *c)
     delete c;
 }
 
+sr_status sr_set_option(sr_ctx *c, int option, int value)
+{
+    if (!c)
+        return fail(SR_EINVAL, "sr_set_option: ctx is NULL");
+    if (option == SR_OPT_BOOL_TENSOR && value >= 0 && value <= 2) {
+        c->bool_tc_mode = value;
+        return SR_OK;
+    }
+    return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
+}
+
 sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size_t *bytes)
 {
     if (!bytes)
@@ -190,8 +201,10 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
     if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_SQUARING) {
         const int64_t rw = row_units(dtype, D) * u32_per_unit(dtype);
         const int64_t ldw = (rw + 3) / 4 * 4;
-        *bytes = (size_t)(2 * D * ldw * 4);
+        *bytes = (size_t)(2 * D * ldw * 4) + bool_tc_workspace(D, D, D);   // squares + tensor-core operands
     }
+    if (op == SR_OP_BOOL_MUL && is_bool(dtype))
+        *bytes = bool_tc_workspace(D, D, D);
     return SR_OK;
 }
 
@@ -279,8 +292,16 @@ sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int6
     return launch_antidist_mul(a, dtype, vec, S(stream));
 }
 
+// tensor-core path when the context allows it and has the workspace
+static bool use_tc(const sr_ctx *c, int64_t R, int64_t K, int64_t N, size_t ws_avail)
+{
+    if (!c || c->bool_tc_mode == 0 || R < 1 || (c->bool_tc_mode == 1 && K < 1024)) return false;
+    return bool_tc_workspace(R, K, N) <= ws_avail && bool_tc_available();
+}
+
 static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
-                               int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, cudaStream_t s)
+                               int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, cudaStream_t s,
+                               sr_ctx *ctx = nullptr, void *ws = nullptr, size_t ws_bytes = 0)
 {
     const int u = u32_per_unit(dtype);
     BoolArgs a;
@@ -293,11 +314,13 @@ static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_
     a.accumulate = accumulate ? 1 : 0;
     a.skip0 = 0x7fffffff; a.skipw = 0;
     a.skip0w = 0x7fffffff; a.skipww = 0;
+    if (use_tc(ctx, R, K, N, ws_bytes))
+        return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, s);
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
     return launch_bool_mul(a, vec, s);
 }
 
-sr_status bool_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                    int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
 {
     const char *fn = "bool_mul";
@@ -312,7 +335,9 @@ sr_status bool_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t 
     const Range rc = span(C, ldc, R, N, dtype);
     if (overlap(rc, span(A, lda, R, K, dtype)) || overlap(rc, span(B, ldb, K, N, dtype)))
         return fail(SR_EINVAL, "%s: C overlaps A or B (use bool_closure for the in-place form)", fn);
-    return bool_mul_impl(A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate, S(stream));
+    sr_ctx *c = ctx;
+    return bool_mul_impl(A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate, S(stream), c, c ? c->ws : nullptr,
+                         c ? c->ws_bytes : 0);
 }
 
 // ------------------------------------------------------------------ closures
@@ -342,16 +367,14 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
         return launch_bool_closure_warshall(T32, ldt * u, (int)D, rw, vec, S(stream));
     if (method != SR_CLOSURE_SQUARING)
         return fail(SR_EINVAL, "%s: unknown method %d", fn, method);
-    size_t need = 0;
-    SR_TRY(sr_workspace_query(SR_OP_BOOL_CLOSURE, dtype, D, method, &need));
     if (!c)
         return fail(SR_EINVAL, "%s: the squaring method needs a context with workspace", fn);
-    if (c->ws_bytes < need)
-        return fail(SR_ENOMEM, "%s: squaring needs %zu workspace bytes, context has %zu", fn, need, c->ws_bytes);
-    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words
+    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words; any
+    // workspace beyond them holds the tensor-core operands when it is large enough
     const int64_t ldw = ((int64_t)rw + 3) / 4 * 4;
     if ((size_t)(2 * D * ldw * 4) > c->ws_bytes)
-        return fail(SR_ENOMEM, "%s: workspace too small for padded rows", fn);
+        return fail(SR_ENOMEM, "%s: squaring needs at least %zu workspace bytes, context has %zu", fn,
+                    (size_t)(2 * D * ldw * 4), c->ws_bytes);
     uint32_t *M = static_cast<uint32_t *>(c->ws);
     uint32_t *M2 = M + D * ldw;
     cudaStream_t s = S(stream);
@@ -359,6 +382,9 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     SR_TRY(launch_bool_identity_or(M, ldw, (int)D, s));                  // M = I ⊕ A
     int m = 0;
     while (((int64_t)1 << m) < (D - 1 > 1 ? D - 1 : 1)) ++m;
+    void *tcws = static_cast<char *>(c->ws) + 2 * D * ldw * 4;
+    const size_t tcbytes = c->ws_bytes - (size_t)(2 * D * ldw * 4);
+    const bool tcpath = use_tc(c, D, D, D, tcbytes);
     auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z) -> sr_status {
         BoolArgs a;
         a.A = X; a.B = Y; a.C = Z;
@@ -368,6 +394,8 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
         a.accumulate = 0;
         a.skip0 = 0x7fffffff; a.skipw = 0;
         a.skip0w = 0x7fffffff; a.skipww = 0;
+        if (tcpath)
+            return launch_bool_mul_tc(a, tcws, tcbytes, c->d_status, s);
         const bool v = aligned16(X) && aligned16(Y) && ((ldx & 3) == 0) && ((ldy & 3) == 0);
         return launch_bool_mul(a, v, s);
     };

@@ -265,8 +265,10 @@ static sr_status enqueue_request(ServeState &st, Job &job, cudaStream_t s)
             SR_TRY(launch_antidist_closure(T, ld, (int)D, t, true, s));
         } else if (r.method == SR_CLOSURE_SQUARING) {
             sr_ctx tmp;                                   // workspace = this request's arena block
+            const int64_t rw = units_of(t, D) * u32;
             tmp.ws = dptr(offs[k++]);
-            tmp.ws_bytes = (size_t)1 << 62;
+            tmp.ws_bytes = (size_t)(2 * D * ((rw + 3) / 4 * 4) * 4);
+            tmp.bool_tc_mode = 0;                         // the block holds the two squares only
             SR_TRY(bool_closure(&tmp, T, ld, D, t, SR_CLOSURE_SQUARING, s));
         } else {
             SR_TRY(launch_bool_closure_warshall(reinterpret_cast<uint32_t *>(T), ld * u32, (int)D,

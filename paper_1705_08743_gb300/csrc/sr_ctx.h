@@ -21,6 +21,7 @@ struct sr_ctx {
     size_t ws_bytes = 0;
     int *d_status = nullptr;      // device status words: [0] error code, [1] where
     int spin_limit = sr::kDefaultSpinLimit;
+    int bool_tc_mode = 1;         // tensor-core Boolean products: 0 never, 1 when K >= 1024, 2 when possible
     sr::ServeState *serve = nullptr;
     std::map<std::string, std::array<int, 3>> tune;   // autotuned batch configurations by signature
 };

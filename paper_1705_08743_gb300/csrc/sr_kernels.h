@@ -56,6 +56,10 @@ struct BoolArgs {
 };
 // shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
 sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape = 0);
+// Tensor-core Boolean product (bool_tc.cu): workspace bytes, availability, launch.
+size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N);
+bool bool_tc_available();
+sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
                            int rw, int num_sms, cudaStream_t s);

@@ -171,3 +171,34 @@ def test_cfg3_bool_closure_full_16384(sq_ctx):
     finally:
         sr.sr_destroy(ctx)
     assert np.array_equal(got2, ref)
+
+
+# ---------------------------------------------------------------- tensor-core path
+@pytest.mark.parametrize("shape", [(128, 128, 256), (128, 1024, 256), (200, 300, 257), (333, 2100, 700),
+                                   (1, 64, 1), (1000, 4096, 1000)])
+@pytest.mark.parametrize("w", [32, 64])
+def test_bool_mul_tensor_path(shape, w):
+    """Count on the tensor cores, then test > 0: bit-exact against the oracle,
+    with and without accumulation, forced on for every shape."""
+    import paper_1705_08743_gb300 as sr
+    R, K, N = shape
+    rng = np.random.default_rng(R * 31 + K + N)
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_MUL, sr.SR_BOOL_W64, max(R, K, N)) + 4096)
+    sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 2)
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    try:
+        for p in [0.01, 0.2]:
+            A, B = rand_bool(rng, R, K, p), rand_bool(rng, K, N, p)
+            Ad, Bd = to_dev(packed(A, w)), to_dev(packed(B, w))
+            C0 = rand_bool(rng, R, N, 0.1)
+            for acc in (0, 1):
+                Cd = to_dev(packed(C0, w)) if acc else to_dev(np.zeros_like(packed(C0, w)))
+                sr.bool_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, dt, acc)
+                sr.sr_stream_status(ctx)
+                got = unpacked(to_host(Cd, np.uint64 if w == 64 else np.uint32), w, N)
+                want = oracle.mul(A, B, 1)
+                if acc:
+                    want = np.maximum(C0, want)
+                assert np.array_equal(got, want), (p, acc)
+    finally:
+        sr.sr_destroy(ctx)
