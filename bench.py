@@ -516,6 +516,120 @@ class Cfg5:
         return {"ops": 0, "seconds": 1.0, "sample": "not measured for the served stream"}
 
 
+class CfgBool:
+    """Boolean workloads.  cfg1: product 512x512x512, Bernoulli(0.02), 32 columns per
+    word (latency-bound; reported in us).  cfg3: transitive closure D=16384, 64-bit
+    words, DAG (i<j, p=2/D) union random digraph (mean out-degree 1.5), seed 2; the
+    step packs the dense 0/1 input and closes it by blocked Warshall; the squaring
+    form (A ⊗ (I ⊕ A)^(2^14), 15 products of 16384^3 on the tensor cores) is timed
+    beside it."""
+
+    only = ""
+
+    def __init__(self, kind):
+        self.kind = kind
+        self.dtype = "bits"
+        if kind == "cfg1":
+            self.D, self.name = 512, "bool_mul 512x512x512, Bernoulli(0.02), seed 0, 32 columns per uint32"
+        else:
+            self.D, self.name = 16384, ("bool_closure D=16384 bit-packed uint64: DAG (i<j, p=2/D) union random "
+                                        "digraph (p=1.5/D), seed 2; pack + blocked Warshall")
+        self.ops = float(self.D) ** 3
+
+    def host_inputs(self):
+        import synth
+        if self.kind == "cfg1":
+            return synth.cfg1_bool_product()
+        return synth.cfg3_bool_closure(self.D), None
+
+    def setup_device(self, A, B, dev):
+        import torch
+        import paper_1705_08743_gb300 as sr
+        self.sr = sr
+        D = self.D
+        self.w = 32 if self.kind == "cfg1" else 64
+        self.dt = sr.SR_BOOL_W32 if self.w == 32 else sr.SR_BOOL_W64
+        tdt = torch.int32 if self.w == 32 else torch.int64
+        self.nw = D // self.w
+        self.dense = torch.from_numpy(A).to(dev)
+        self.T = torch.zeros((D, self.nw), dtype=tdt, device=dev)
+        if self.kind == "cfg1":
+            self.denseB = torch.from_numpy(B).to(dev)
+            self.A = torch.zeros_like(self.T)
+            self.B = torch.zeros_like(self.T)
+            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt)
+            sr.bool_pack(None, self.denseB, D, self.B, self.nw, D, D, self.dt)
+            self.ctx = None
+        else:
+            self.ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, self.dt, D,
+                                                                          sr.SR_CLOSURE_SQUARING))
+        self.mul_events = []
+
+    def step(self, stream, record_mul=False):
+        import torch
+        sr, D, s = self.sr, self.D, stream.cuda_stream
+        if record_mul:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        if self.kind == "cfg1":
+            sr.bool_mul(None, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
+        else:
+            sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
+            sr.bool_closure(None, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_WARSHALL, s)
+        if record_mul:
+            e1.record(stream)
+            self.mul_events.append((e0, e1))
+
+    def squaring_ms(self, stream, reps=2):
+        import torch
+        sr, D, s = self.sr, self.D, stream.cuda_stream
+        ts = []
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
+            sr.bool_closure(self.ctx, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_SQUARING, s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    def e2e_setup(self, A, B):
+        import torch
+        self.hA = torch.from_numpy(A).pin_memory()
+        self.hT = torch.empty(tuple(self.T.shape), dtype=self.T.dtype).pin_memory()
+        self.h2d = self.hA.numel()
+        self.d2h = self.hT.numel() * self.hT.element_size()
+        if self.kind == "cfg1":
+            self.hB = torch.from_numpy(B).pin_memory()
+            self.h2d *= 2
+
+    def e2e_step(self, stream):
+        sr, D, s = self.sr, self.D, stream.cuda_stream
+        self.dense.copy_(self.hA, non_blocking=True)
+        if self.kind == "cfg1":
+            self.denseB.copy_(self.hB, non_blocking=True)
+            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt, s)
+            sr.bool_pack(None, self.denseB, D, self.B, self.nw, D, D, self.dt, s)
+        self.step(stream)
+        self.hT.copy_(self.T, non_blocking=True)
+
+    def cpu_sample(self, A, B):
+        import oracle
+        t0 = time.perf_counter()
+        if self.kind == "cfg1":
+            oracle.bool_mul_w64(oracle.pack_bits(A), oracle.pack_bits(B), self.D)
+            ops, what = float(self.D) ** 3, "oracle packed product 512^3"
+        else:
+            rows = 2048
+            Ap = oracle.pack_bits(A)
+            oracle.bool_mul_w64(Ap[:rows], Ap, self.D)
+            ops, what = float(rows) * self.D * self.D, f"oracle packed product, rows 0..{rows - 1} of 16384^3"
+        dt = time.perf_counter() - t0
+        return {"ops": ops, "seconds": dt, "sample": what}
+
+
 WORKLOADS = {
     "cfg2": lambda: Cfg2(4096, "u8"),
     "cfg2-8192": lambda: Cfg2(8192, "u8"),
@@ -523,6 +637,8 @@ WORKLOADS = {
     "cfg4": lambda: Cfg4(2000),
     "cfg4-200": lambda: Cfg4(200),
     "cfg5": lambda: Cfg5(),
+    "cfg1": lambda: CfgBool("cfg1"),
+    "cfg3": lambda: CfgBool("cfg3"),
 }
 
 
@@ -625,8 +741,8 @@ def run_ours(args, world, rank, local):
 
     # pipe peak of the product's inner operation, measured on this GPU now
     with torch.cuda.stream(stream):
-        pk_ms, pk_ips, pk_ops = sr.sr_peak_probe(sr.SR_PEAK_DPX_S16X2 if wl.dtype == "u8" else sr.SR_PEAK_U16_PAIR,
-                                                 iters=8192, blocks_per_sm=8, stream=stream.cuda_stream)
+        probe = {"u8": sr.SR_PEAK_DPX_S16X2, "u16": sr.SR_PEAK_U16_PAIR}.get(wl.dtype, sr.SR_PEAK_LOP3)
+        pk_ms, pk_ips, pk_ops = sr.sr_peak_probe(probe, iters=8192, blocks_per_sm=8, stream=stream.cuda_stream)
 
     pre = getattr(wl, "pre_step", lambda st: None)
     with torch.cuda.stream(stream):
@@ -692,6 +808,18 @@ def run_ours(args, world, rank, local):
         return
     if args.only:
         print(json.dumps({"only": args.only, "ms_per_step": ms_per_step, "gpu_launches": launches}), flush=True)
+        return
+    if isinstance(wl, CfgBool):
+        t = sum(mul_ms) / len(mul_ms)
+        extra = {"step_us": t * 1e3}
+        if wl.kind == "cfg3":
+            extra["squaring_ms"] = wl.squaring_ms(stream)
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bits", "data": "synthetic",
+            "config": {"workload": wl.name, "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "boolean": extra, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}), flush=True)
         return
     if isinstance(wl, Cfg4):
         print(json.dumps(cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, launches, clk,

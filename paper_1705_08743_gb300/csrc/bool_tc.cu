@@ -35,6 +35,7 @@ constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK;
 constexpr size_t SMEM = 1024 + (size_t)STAGES * (A_BYTES + B_BYTES) + 128;
 constexpr int TMEM_COLS = 256;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;     // tries per wait before giving up
+constexpr int GROUP_M = 16;                  // tile rows per rasterisation group
 }  // namespace tc
 
 struct BoolTcArgs {
@@ -43,6 +44,7 @@ struct BoolTcArgs {
     int R, N;             // rows of C; bits per row of C (pad bits written 0)
     int ncw;              // 32-bit words per row of C to write
     int nkb;              // K slices of BK bytes
+    int tiles_m, tiles_n; // output tiles (BM rows, BN columns)
     int accumulate;
     int *status;          // nonzero after a bounded wait gave up (may be null)
 };
@@ -119,7 +121,19 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     __shared__ int failed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row0 = blockIdx.y * tc::BM, ncol0 = blockIdx.x * tc::BN;
+    // grouped rasterisation: consecutive CTAs walk GROUP_M tile rows before moving to the
+    // next tile column, so a wave's A and B panels stay resident in L2
+    int tm, tn;
+    {
+        const int b = blockIdx.x, tiles_m = p.tiles_m, tiles_n = p.tiles_n;
+        const int per_group = tc::GROUP_M * tiles_n;
+        const int g = b / per_group, first_m = g * tc::GROUP_M;
+        const int gm = min(tc::GROUP_M, tiles_m - first_m);
+        const int r = b - g * per_group;
+        tm = first_m + r % gm;
+        tn = r / gm;
+    }
+    const int row0 = tm * tc::BM, ncol0 = tn * tc::BN;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES), done = smem_u32(bars + 2 * tc::STAGES);
 
     if (tid == 0) {
@@ -352,8 +366,12 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     p.nkb = Kp / tc::BK;
     p.accumulate = a.accumulate;
     p.status = status;
-    dim3 grid((a.ncw + tc::BN / 32 - 1) / (tc::BN / 32), (a.R + tc::BM - 1) / tc::BM);
-    bool_tc_kernel<<<grid, 128, tc::SMEM, s>>>(mA, mB, p);
+    p.tiles_n = (a.ncw + tc::BN / 32 - 1) / (tc::BN / 32);
+    p.tiles_m = (a.R + tc::BM - 1) / tc::BM;
+    const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
+    if (tiles > 0x7fffffffLL)
+        return fail(SR_EINVAL, "bool_mul (tensor path): too many tiles");
+    bool_tc_kernel<<<(unsigned)tiles, 128, tc::SMEM, s>>>(mA, mB, p);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;

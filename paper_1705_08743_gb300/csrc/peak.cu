@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) peak_kernel(int iters, uint32_t seed, uin
                 else if (OP == SR_PEAK_U16_PAIR)
                     nxt[j] = __viaddmax_u16x2(vmax_u16x2(x, a0), a1, acc[j]);
                 else if (OP == SR_PEAK_LOP3)
-                    nxt[j] = acc[j] | (x & (a0 ^ (uint32_t)s));
+                    nxt[j] = acc[j] | (x & acc[(j + 2) & 7]);      // one three-input LOP3
                 else
                     nxt[j] = acc[j] + x;
             }
