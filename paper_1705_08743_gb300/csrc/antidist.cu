@@ -34,6 +34,13 @@ namespace sr {
 
 __device__ __forceinline__ int remap(int x, int skip0, int skipw) { return x < skip0 ? x : x + skipw; }
 
+// u8 product kernel: accumulators hold acc + 255 in each 16-bit lane and the broadcast
+// operand holds a (not a − 255), so max(acc + 255, a + b) = max(acc, a + b − 255) + 255
+// with the same single add-max per lane pair and a one-instruction byte broadcast at
+// staging.  Lanes stay in [255, 510] (acc >= 0), so adding or removing 255 per lane
+// never carries or borrows across lanes.
+constexpr uint32_t kShift8 = 0x00FF00FFu;
+
 // -------------------------------------------------------------------------
 // 16-byte chunk loads with zero fill outside [0, nrow) × [0, ncol)
 // -------------------------------------------------------------------------
@@ -155,7 +162,12 @@ antidist_mul_kernel(MulArgs p)
 #pragma unroll
             for (int t = 0; t < CH; ++t) {
                 uint32_t a0, a1;
-                KD::bcast(chunk_elem<E>(ra[u], t), a0, a1);
+                if (sizeof(E) == 1) {      // raw byte in both lanes (the accumulator carries the −S)
+                    a0 = __byte_perm(u4get(ra[u], t / 4), 0u, 0x4040 | (t % 4) | ((t % 4) << 8));
+                    a1 = 0u;
+                } else {
+                    KD::bcast(chunk_elem<E>(ra[u], t), a0, a1);
+                }
                 const int k = kc * CH + t;
                 sA0[(buf * BK + k) * BM + i] = a0;
                 if (KD::AW == 2)
@@ -225,8 +237,8 @@ antidist_mul_kernel(MulArgs p)
                     const uint32_t *row = reinterpret_cast<const uint32_t *>(sC + li * CROW);
                     if (sizeof(E) == 1) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(row + lc / 4);
-                        acc[i][g * 4] = u8x2_lo(v.x); acc[i][g * 4 + 1] = u8x2_hi(v.x);
-                        acc[i][g * 4 + 2] = u8x2_lo(v.y); acc[i][g * 4 + 3] = u8x2_hi(v.y);
+                        acc[i][g * 4] = u8x2_lo(v.x) + kShift8; acc[i][g * 4 + 1] = u8x2_hi(v.x) + kShift8;
+                        acc[i][g * 4 + 2] = u8x2_lo(v.y) + kShift8; acc[i][g * 4 + 3] = u8x2_hi(v.y) + kShift8;
                     } else {
                         const uint4 v = *reinterpret_cast<const uint4 *>(row + lc / 2);
                         acc[i][g * 4] = v.x; acc[i][g * 4 + 1] = v.y; acc[i][g * 4 + 2] = v.z; acc[i][g * 4 + 3] = v.w;
@@ -239,7 +251,7 @@ antidist_mul_kernel(MulArgs p)
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < NP; ++j) acc[i][j] = 0u;
+                for (int j = 0; j < NP; ++j) acc[i][j] = sizeof(E) == 1 ? kShift8 : 0u;
         }
 
         sstore(0);
@@ -298,7 +310,8 @@ antidist_mul_kernel(MulArgs p)
                 E *dst = C + (int64_t)pr * p.ldc + remap(c, p.cskip0, p.cskipw);
                 const uint32_t *q = &acc[i][g * 4];
                 if (sizeof(E) == 1) {
-                    const uint32_t w0 = pack_u8x4(q[0], q[1]), w1 = pack_u8x4(q[2], q[3]);
+                    const uint32_t w0 = pack_u8x4(q[0] - kShift8, q[1] - kShift8);
+                    const uint32_t w1 = pack_u8x4(q[2] - kShift8, q[3] - kShift8);
                     if (VEC && c + 8 <= p.N) {
                         *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
                     } else {
