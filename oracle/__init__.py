@@ -67,6 +67,9 @@ def _load():
                 "or_bool_warshall_w64": (None, [_p, _i64, _i64]),
                 "or_bool_closure_row_w64": (None, [_p, _i64, _i64, _i64, _p]),
                 "or_encode_antidist": (None, [_p, _i64, _u32, _p]),
+                "or_dist_mul": (None, [_p, _p, _p, _i64, _i64, _i64, _u32, ctypes.c_int]),
+                "or_dist_closure": (None, [_p, _i64, _u32]),
+                "or_entrywise": (None, [ctypes.c_int, _p, _p, _p, _i64, _u32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -196,3 +199,33 @@ def bool_closure_row_w64(A, src: int) -> np.ndarray:
     row = np.zeros(words64(D), np.uint64)
     _load().or_bool_closure_row_w64(_ptr(A), A.shape[1], D, src, _ptr(row))
     return row
+
+
+# ------------------------------------------------------------ distance form
+
+def dist_mul(X, Y, S: int, Z=None) -> np.ndarray:
+    """(Z if given else all-S) ∧ (X + Y) with min and saturating addition at S."""
+    X, Y = _u32c(X), _u32c(Y)
+    R, K = X.shape
+    N = Y.shape[1]
+    out = np.full((R, N), S, np.uint32) if Z is None else _u32c(Z).copy()
+    _load().or_dist_mul(_ptr(X), _ptr(Y), _ptr(out), R, K, N, S, 0 if Z is None else 1)
+    return out
+
+
+def dist_closure(A, S: int) -> np.ndarray:
+    """Floyd on saturating distances, diagonal = shortest cycle (not reset to 0)."""
+    T = _u32c(A).copy()
+    _load().or_dist_closure(_ptr(T), T.shape[0], S)
+    return T
+
+
+ENTRYWISE = {"and": 0, "or": 1, "xor": 2, "not": 3}
+
+
+def entrywise(op: str, A, B=None, S: int = 255) -> np.ndarray:
+    A = _u32c(A)
+    Bc = None if B is None else _u32c(B)
+    out = np.zeros_like(A)
+    _load().or_entrywise(ENTRYWISE[op], _ptr(A), None if Bc is None else _ptr(Bc), _ptr(out), A.size, S)
+    return out

@@ -322,3 +322,76 @@ void or_encode_antidist(const uint32_t *W, i64 n, uint32_t S, uint32_t *out)
     for (i64 t = 0; t < n; ++t)
         out[t] = (W[t] == 0 || W[t] >= S) ? 0u : S - W[t];
 }
+
+/* ------------------------------------------------------------------------ */
+/* Distance matrices (Section 4, the dual form; Conclusion, dransclose)      */
+/* ------------------------------------------------------------------------ */
+
+/* Saturating distance addition on {0..S}: min(x + y, S). */
+static inline uint32_t dist_plus(uint32_t x, uint32_t y, uint32_t S)
+{
+    uint64_t s = (uint64_t)x + y;
+    return s >= S ? S : (uint32_t)s;
+}
+
+/*
+ * Distance product ("funny" product, Section 3 remark; Section 4 dual with ∧ in
+ * place of ∨ and saturating addition in place of ⊗): Z_ij = min over k of
+ * min(X_ik + Y_kj, S), combined by min with Z when accumulating.  S plays the
+ * role of infinity (the neutral element of min).
+ */
+void or_dist_mul(const uint32_t *X, const uint32_t *Y, uint32_t *Z, i64 R, i64 K, i64 N, uint32_t S,
+                 int accumulate)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < R; ++i)
+        for (i64 j = 0; j < N; ++j) {
+            uint32_t z = accumulate ? Z[i * N + j] : S;
+            for (i64 k = 0; k < K; ++k) {
+                uint32_t d = dist_plus(X[i * K + k], Y[k * N + j], S);
+                if (d < z) z = d;
+            }
+            Z[i * N + j] = z;
+        }
+}
+
+/*
+ * Floyd's algorithm on distances, in place, without setting the diagonal to 0:
+ * T_ii ends as the shortest cycle through i ("minimum loop lengths on the
+ * diagonal", Conclusion).  Lengths saturate at S.
+ */
+void or_dist_closure(uint32_t *T, i64 D, uint32_t S)
+{
+    for (i64 k = 0; k < D; ++k) {
+        const uint32_t *Tk = T + k * D;
+#pragma omp parallel for schedule(static)
+        for (i64 i = 0; i < D; ++i) {
+            if (i == k) continue;              /* row k is unchanged in step k */
+            uint32_t a = T[i * D + k];
+            if (a >= S) continue;
+            uint32_t *Ti = T + i * D;
+            for (i64 j = 0; j < D; ++j) {
+                uint32_t d = dist_plus(a, Tk[j], S);
+                if (d < Ti[j]) Ti[j] = d;
+            }
+        }
+    }
+}
+
+/*
+ * Entrywise operations (Conclusion table): op 0: a & b = min(a, b);
+ * op 1: a | b = max(a, b); op 2: a ^ b = |a − b|; op 3: ~a = S − a (b unused).
+ * For S = 1 these are the Boolean AND, OR, XOR, NOT.
+ */
+void or_entrywise(int op, const uint32_t *A, const uint32_t *B, uint32_t *out, i64 n, uint32_t S)
+{
+    for (i64 t = 0; t < n; ++t) {
+        uint32_t a = A[t], b = B ? B[t] : 0;
+        switch (op) {
+        case 0: out[t] = a < b ? a : b; break;
+        case 1: out[t] = a > b ? a : b; break;
+        case 2: out[t] = a > b ? a - b : b - a; break;
+        default: out[t] = S - a; break;
+        }
+    }
+}

@@ -341,3 +341,67 @@ def test_generator_density():
     assert min(sizes) >= 32 and max(sizes) <= 1024
     mean_cube = np.mean(np.array(sizes, dtype=np.float64) ** 3)
     assert 0.8 < mean_cube / synth.expected_log_uniform_cube(32, 1024) < 1.25
+
+
+# ------------------------------------------------------------------ distance form (f1) and entrywise (f3)
+
+def brute_dist_closure(Dm, S):
+    """min over simple paths (i != j) / simple cycles (i == j) of min(length, S);
+    entries >= S are no edge."""
+    Dm = np.asarray(Dm, dtype=np.int64)
+    n = Dm.shape[0]
+    T = np.full((n, n), S, dtype=np.int64)
+
+    def dfs(src, v, length, seen):
+        for u in range(n):
+            w = Dm[v, u]
+            if w >= S:
+                continue
+            L = min(length + w, S)
+            if u == src:
+                T[src, src] = min(T[src, src], L)
+            elif u not in seen:
+                T[src, u] = min(T[src, u], L)
+                dfs(src, u, L, seen | {u})
+
+    for i in range(n):
+        dfs(i, i, 0, {i})
+    return T.astype(np.uint32)
+
+
+@pytest.mark.parametrize("S", [255, 65535])
+def test_dist_mul_by_de_morgan_and_brute_force(S):
+    rng = np.random.default_rng(51)
+    A, B = rand_mat(rng, 9, 13, S, density=0.6), rand_mat(rng, 13, 7, S, density=0.6)
+    dA, dB = (S - A.astype(np.int64)).astype(np.uint32), (S - B.astype(np.int64)).astype(np.uint32)
+    # De Morgan (Section 4): S − (A ⊗ B) = (S − A) + (S − B) in the distance form
+    assert np.array_equal(oracle.dist_mul(dA, dB, S), (S - oracle.mul(A, B, S).astype(np.int64)).astype(np.uint32))
+    assert np.array_equal(oracle.dist_mul(dA, dB, S), minplus_sat(dA, dB, S))
+    Z = rand_mat(rng, 9, 7, S, density=0.9)
+    assert np.array_equal(oracle.dist_mul(dA, dB, S, Z=Z), np.minimum(Z, minplus_sat(dA, dB, S)))
+
+
+@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("D", [1, 4, 7])
+def test_dist_closure_brute_force_and_de_morgan(S, D):
+    rng = np.random.default_rng(60 + D)
+    A = rand_mat(rng, D, D, S, density=0.5, lo=S - S // 3)
+    dA = (S - A.astype(np.int64)).astype(np.uint32)        # absent edge (a = 0) -> S = infinity
+    T = oracle.dist_closure(dA, S)
+    assert np.array_equal(T, brute_dist_closure(dA, S))
+    assert np.array_equal(T, (S - oracle.warshall(A, S).astype(np.int64)).astype(np.uint32))
+
+
+def test_entrywise_table():
+    # Conclusion table: & = min, | = max, ^ = |a − b|, ~ = S − a
+    a = np.array([[0, 5, 255, 100]], np.uint32)
+    b = np.array([[7, 5, 0, 200]], np.uint32)
+    assert oracle.entrywise("and", a, b).tolist() == [[0, 5, 0, 100]]
+    assert oracle.entrywise("or", a, b).tolist() == [[7, 5, 255, 200]]
+    assert oracle.entrywise("xor", a, b).tolist() == [[7, 0, 255, 100]]
+    assert oracle.entrywise("not", a, S=255).tolist() == [[255, 250, 0, 155]]
+    bits_a, bits_b = np.array([[0, 0, 1, 1]], np.uint32), np.array([[0, 1, 0, 1]], np.uint32)
+    assert oracle.entrywise("and", bits_a, bits_b, S=1).tolist() == [[0, 0, 0, 1]]
+    assert oracle.entrywise("or", bits_a, bits_b, S=1).tolist() == [[0, 1, 1, 1]]
+    assert oracle.entrywise("xor", bits_a, bits_b, S=1).tolist() == [[0, 1, 1, 0]]
+    assert oracle.entrywise("not", bits_a, S=1).tolist() == [[1, 1, 0, 0]]
