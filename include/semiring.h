@@ -70,7 +70,8 @@ typedef enum {
     SR_OP_ANTIDIST_MUL = 0,
     SR_OP_BOOL_MUL = 1,
     SR_OP_ANTIDIST_CLOSURE = 2,
-    SR_OP_BOOL_CLOSURE = 3
+    SR_OP_BOOL_CLOSURE = 3,
+    SR_OP_DIST_MUL = 4
 } sr_op;
 
 typedef struct sr_ctx sr_ctx;
@@ -292,6 +293,40 @@ sr_status sr_serve_stats(sr_ctx *ctx, sr_serve_stats_t *out);
  *    first call before any stream capture.
  *  - Calls no cudaMalloc/cudaFree or any allocating routine. */
 sr_status bool_closure_squaring_noalloc(void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------- distance form (Section 4 dual; Conclusion) */
+
+/* Distance matrices: entry = length d in {0..S}, S standing for infinity (no
+ * path or length >= S).  ∧ = min replaces ∨ and saturating addition replaces ⊗
+ * (Section 4: the dual operations; De Morgan: S − (A ⊗ B) = (S − A) + (S − B)).
+ *   dist_mul:     C := (accumulate ? C : all-S) ∧ (A + B),
+ *                 (A + B)_ij = min over k of min(A_ik + B_kj, S);
+ *                 computed as S − antidist_mul(S − A, S − B); needs ctx workspace of
+ *                 sr_workspace_query(SR_OP_DIST_MUL, dtype, max(R, K, N), 0) bytes.
+ *   dist_closure: in place, T := shortest saturated lengths of paths with >= 1 edge;
+ *                 T_ii = shortest cycle through i (the Conclusion's dransclose, minimum
+ *                 loop lengths on the diagonal); computed as S − antidist_closure(S − T)
+ *                 in place, no workspace.
+ * dtype SR_U8 or SR_U16. */
+sr_status dist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                   int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream);
+sr_status dist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------- entrywise (Conclusion table) */
+
+typedef enum {
+    SR_EW_AND = 0,     /* a & b = min(a, b)   (Boolean: AND) */
+    SR_EW_OR = 1,      /* a | b = max(a, b)   (Boolean: OR)  */
+    SR_EW_XOR = 2,     /* a ^ b = |a − b|     (Boolean: XOR) */
+    SR_EW_NOT = 3      /* ~a = S − a          (Boolean: NOT; B unused, may be NULL) */
+} sr_entrywise_op;
+
+/* C := A op B entrywise, R×N, any dtype (Boolean: words, pad bits written 0).
+ * C may be A or B (in place). */
+sr_status sr_entrywise(sr_ctx *ctx, int op, const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
+                       int64_t ldc, int64_t R, int64_t N, sr_dtype dtype, void *stream);
+/* Reflexive closure from the non-reflexive one: T := I ⊕ T (diagonal set to S or to 1). */
+sr_status sr_reflexive(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
 
 /* ---------------------------------------------------------------- diagnostics */
 

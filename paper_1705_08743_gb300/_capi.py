@@ -30,6 +30,8 @@ SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
 SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
 SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD = range(4)
 SR_OPT_BOOL_TENSOR = 1
+SR_OP_DIST_MUL = 4
+SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 
 STATUS_NAMES = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ETIMEOUT",
                 5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND"}
@@ -106,6 +108,10 @@ _SIGS = {
     "sr_batch_info": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
     "sr_batch_destroy": (None, [_vp]),
     "sr_batched": (_st, [_vp, ctypes.POINTER(sr_desc), _int, _vp]),
+    "dist_mul": (_st, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp]),
+    "dist_closure": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
+    "sr_entrywise": (_st, [_vp, _int, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp]),
+    "sr_reflexive": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
     "sr_serve_start": (_st, [_vp, ctypes.POINTER(sr_serve_config)]),
     "sr_serve_stop": (_st, [_vp]),
     "sr_submit": (_st, [_vp, ctypes.POINTER(sr_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -363,3 +369,21 @@ def sr_serve_stats(ctx):
     st = sr_serve_stats_t()
     _check(lib.sr_serve_stats(ctx, ctypes.byref(st)), "sr_serve_stats")
     return {f: getattr(st, f) for f, _ in sr_serve_stats_t._fields_}
+
+
+def dist_mul(ctx, A, lda, B, ldb, C, ldc, R, K, N, dtype, accumulate=0, stream=None):
+    _check(lib.dist_mul(ctx, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, R, K, N, dtype, int(accumulate),
+                        _stream(stream)), "dist_mul")
+
+
+def dist_closure(ctx, T, ldt, D, dtype, stream=None):
+    _check(lib.dist_closure(ctx, _ptr(T), ldt, D, dtype, _stream(stream)), "dist_closure")
+
+
+def sr_entrywise(ctx, op, A, lda, B, ldb, C, ldc, R, N, dtype, stream=None):
+    _check(lib.sr_entrywise(ctx, op, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, R, N, dtype, _stream(stream)),
+           "sr_entrywise")
+
+
+def sr_reflexive(ctx, T, ldt, D, dtype, stream=None):
+    _check(lib.sr_reflexive(ctx, _ptr(T), ldt, D, dtype, _stream(stream)), "sr_reflexive")

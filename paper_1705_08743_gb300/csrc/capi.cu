@@ -205,6 +205,8 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
     }
     if (op == SR_OP_BOOL_MUL && is_bool(dtype))
         *bytes = bool_tc_workspace(D, D, D);
+    if (op == SR_OP_DIST_MUL && is_anti(dtype))
+        *bytes = (size_t)(2 * D * ((D + 15) / 16 * 16) * esize(dtype) + 1024);
     return SR_OK;
 }
 
@@ -405,6 +407,89 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     }
     SR_TRY(mul32(T32, ldt * u, M, ldw, M2));                              // A ⊗ (I ⊕ A)^(2^m)
     return launch_copy_rows(M2, ldw, T32, ldt * u, (int)D, rw, s);
+}
+
+// ------------------------------------------------------------------ distance form
+sr_status dist_mul(sr_ctx *c, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                   int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
+{
+    const char *fn = "dist_mul";
+    if (!is_anti(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "K", K));
+    SR_TRY(check_dim(fn, "N", N));
+    SR_TRY(check_mat(fn, "A", A, lda, R, K, dtype));
+    SR_TRY(check_mat(fn, "B", B, ldb, K, N, dtype));
+    SR_TRY(check_mat(fn, "C", C, ldc, R, N, dtype));
+    const Range rc = span(C, ldc, R, N, dtype);
+    if (overlap(rc, span(A, lda, R, K, dtype)) || overlap(rc, span(B, ldb, K, N, dtype)))
+        return fail(SR_EINVAL, "%s: C overlaps A or B", fn);
+    const int es = esize(dtype);
+    const int64_t ka = (K + 15) / 16 * 16, na = (N + 15) / 16 * 16;   // 16-byte aligned rows
+    const size_t need = (size_t)((R * ka + K * na) * es) + 512;
+    if (!c || !c->ws || c->ws_bytes < need)
+        return fail(SR_ENOMEM, "%s: needs a context with %zu workspace bytes", fn, need);
+    cudaStream_t s = S(stream);
+    char *Ac = static_cast<char *>(c->ws);
+    char *Bc = Ac + ((R * ka * es + 255) / 256) * 256;
+    // De Morgan (Section 4): A ∧+ B = S − ((S − A) ⊗ (S − B)), and C ∧ X = S − ((S − C) ⊕ (S − X))
+    SR_TRY(launch_entrywise(SR_EW_NOT, A, lda, nullptr, 0, Ac, ka, (int)R, (int)K, dtype, s));
+    SR_TRY(launch_entrywise(SR_EW_NOT, B, ldb, nullptr, 0, Bc, na, (int)K, (int)N, dtype, s));
+    if (accumulate)
+        SR_TRY(launch_entrywise(SR_EW_NOT, C, ldc, nullptr, 0, C, ldc, (int)R, (int)N, dtype, s));
+    MulArgs a;
+    a.A = Ac; a.B = Bc; a.C = C;
+    a.lda = ka; a.ldb = na; a.ldc = ldc;
+    a.R = (int)R; a.K = (int)K; a.N = (int)N;
+    a.accumulate = accumulate ? 1 : 0;
+    a.rskip0 = a.cskip0 = 0x7fffffff;
+    a.rskipw = a.cskipw = 0;
+    a.skip_tile = -1;
+    SR_TRY(launch_antidist_mul(a, dtype, vec_ok(dtype, {{Ac, ka}, {Bc, na}, {C, ldc}}), s));
+    return launch_entrywise(SR_EW_NOT, C, ldc, nullptr, 0, C, ldc, (int)R, (int)N, dtype, s);
+}
+
+sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
+{
+    const char *fn = "dist_closure";
+    if (!is_anti(dtype))
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+    SR_TRY(check_dim(fn, "D", D));
+    SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
+    cudaStream_t s = S(stream);
+    // the anti-distance closure of S − T, complemented back (Section 4, De Morgan)
+    SR_TRY(launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s));
+    SR_TRY(launch_antidist_closure(T, ldt, (int)D, dtype, vec_ok(dtype, {{T, ldt}}), s));
+    return launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s);
+}
+
+// ------------------------------------------------------------------ entrywise
+sr_status sr_entrywise(sr_ctx *, int op, const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
+                       int64_t ldc, int64_t R, int64_t N, sr_dtype dtype, void *stream)
+{
+    const char *fn = "sr_entrywise";
+    if (op < SR_EW_AND || op > SR_EW_NOT)
+        return fail(SR_EINVAL, "%s: unknown op %d", fn, op);
+    if (!is_anti(dtype) && !is_bool(dtype))
+        return fail(SR_EINVAL, "%s: unknown dtype", fn);
+    SR_TRY(check_dim(fn, "R", R));
+    SR_TRY(check_dim(fn, "N", N));
+    SR_TRY(check_mat(fn, "A", A, lda, R, N, dtype));
+    if (op != SR_EW_NOT)
+        SR_TRY(check_mat(fn, "B", B, ldb, R, N, dtype));
+    SR_TRY(check_mat(fn, "C", C, ldc, R, N, dtype));
+    return launch_entrywise(op, A, lda, op == SR_EW_NOT ? nullptr : B, ldb, C, ldc, (int)R, (int)N, dtype, S(stream));
+}
+
+sr_status sr_reflexive(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
+{
+    const char *fn = "sr_reflexive";
+    if (!is_anti(dtype) && !is_bool(dtype))
+        return fail(SR_EINVAL, "%s: unknown dtype", fn);
+    SR_TRY(check_dim(fn, "D", D));
+    SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
+    return launch_reflexive(T, ldt, (int)D, dtype, S(stream));
 }
 
 }  // extern "C"

@@ -85,4 +85,9 @@ struct BatchItem {
 sr_status launch_batched_closure_flat(sr_dtype dt, const BatchGraph *d_graphs, const BatchItem *d_items, int nitems,
                                       int *d_counter, int ctas_per_sm, cudaStream_t s);
 
+// Entrywise operations and the reflexive closure (elementwise.cu).
+sr_status launch_entrywise(int op, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                           int R, int N, sr_dtype dt, cudaStream_t s);
+sr_status launch_reflexive(void *T, int64_t ldt, int D, sr_dtype dt, cudaStream_t s);
+
 }  // namespace sr
