@@ -83,7 +83,7 @@ bool_mul_kernel(BoolArgs p)
         for (int u = 0; u < TNW; ++u) {
             const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
             uint32_t v = 0u;
-            if (p.accumulate && r < p.R && w < p.ncw)
+            if (p.accumulate && p.ksplit == 1 && r < p.R && w < p.ncw)
                 v = p.C[(int64_t)bremap(r, p.skip0, p.skipw) * p.ldc + bremap(w, p.skip0w, p.skipww)];
             acc[i][u] = v;
         }
@@ -128,10 +128,12 @@ bool_mul_kernel(BoolArgs p)
         if (VEC) cp_async_commit();
     };
 
-    const int nkt = (p.K + BKB - 1) / BKB;
-    stage(0, 0);
-    for (int kt = 0; kt < nkt; ++kt) {
-        const int buf = kt & 1;
+    // split-K: CTA z of ksplit takes k-tiles [kt0, kt1) and ORs its partial result into C
+    const int nkt_all = (p.K + BKB - 1) / BKB, per = (nkt_all + p.ksplit - 1) / p.ksplit;
+    const int kt0 = blockIdx.z * per, nkt = min(nkt_all, kt0 + per);
+    if (kt0 < nkt) stage(kt0, 0);
+    for (int kt = kt0; kt < nkt; ++kt) {
+        const int buf = (kt - kt0) & 1;
         if (VEC) cp_async_wait<0>();
         __syncthreads();
         if (kt + 1 < nkt)
@@ -183,7 +185,15 @@ bool_mul_kernel(BoolArgs p)
             const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
             if (w < p.ncw && !(r >= p.kr0 && r < p.kr0 + p.krn && w >= p.kw0 && w < p.kw0 + p.kwn)) {
                 const int pw = bremap(w, p.skip0w, p.skipww);
-                dst[pw] = acc[i][u] & word_mask(pw, p.N);
+                const uint32_t m = word_mask(pw, p.N), v = acc[i][u] & m;
+                if (p.ksplit == 1) {
+                    dst[pw] = v;
+                } else {
+                    // OR is idempotent: partial products combine in any order.  No CTA sets a
+                    // pad bit, so clearing them (z = 0) commutes with the other CTAs' ORs.
+                    if (blockIdx.z == 0 && m != 0xffffffffu) atomicAnd(dst + pw, m);
+                    if (v) atomicOr(dst + pw, v);
+                }
             }
         }
     }
@@ -339,7 +349,7 @@ template <int BM, int BNW, int BKW, int TM, int TNW>
 static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
 {
     using Cfg = BoolCfg<BM, BNW, BKW, TM, TNW>;
-    dim3 grid((a.ncw + BNW - 1) / BNW, (a.R + BM - 1) / BM);
+    dim3 grid((a.ncw + BNW - 1) / BNW, (a.R + BM - 1) / BM, a.ksplit);
     if (grid.y > 65535u)
         return fail(SR_EINVAL, "bool_mul: R too large for the tile grid (%d)", a.R);
     auto kern = vec ? bool_mul_kernel<BM, BNW, BKW, TM, TNW, true> : bool_mul_kernel<BM, BNW, BKW, TM, TNW, false>;
@@ -355,10 +365,25 @@ static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
     return SR_OK;
 }
 
-sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape)
+sr_status launch_bool_mul(const BoolArgs &in, bool vec, cudaStream_t s, int shape)
 {
-    if (a.R <= 0 || a.ncw <= 0)
+    if (in.R <= 0 || in.ncw <= 0)
         return SR_OK;
+    BoolArgs a = in;
+    a.ksplit = 1;
+    if (shape == 0) {
+        // few output tiles (small products): narrower tiles, then split K across CTAs
+        const bool plain = a.skipww == 0 && a.skipw == 0 && a.kr0 < 0;
+        if (a.ncw <= 16 && plain) shape = 2;
+        const int bm = shape == 2 ? 32 : 128, bnw = shape == 2 ? 16 : 64;
+        const int64_t tiles = (int64_t)((a.ncw + bnw - 1) / bnw) * ((a.R + bm - 1) / bm);
+        const int nkt = (a.K + 127) / 128, sms = device_sm_count();
+        if (plain && tiles < sms && nkt >= 2) {
+            a.ksplit = (int)std::min<int64_t>(nkt, (2 * sms + tiles - 1) / tiles);
+            if (!a.accumulate)          // partial results are ORed into a zeroed C
+                SR_CUDA_CHECK(cudaMemset2DAsync(a.C, (size_t)a.ldc * 4, 0, (size_t)a.ncw * 4, (size_t)a.R, s));
+        }
+    }
     if (shape == 1)          // panels a few words wide: 128 rows x 4 words per CTA
         return launch_bool_cfg<128, 4, 4, 4, 4>(a, vec, s);
     if (shape == 2)          // panels a few rows high: 32 rows x 16 words per CTA

@@ -53,6 +53,7 @@ struct BoolArgs {
     int skip0w, skipww;        // excluded word range (words of B and C)
     int kr0 = -1, krn = 0;     // a block of C left unwritten: logical rows [kr0, kr0+krn) ...
     int kw0 = 0, kwn = 0;      // ... and logical words [kw0, kw0+kwn) (kr0 = -1: none)
+    int ksplit = 1;            // CTAs along K (set by launch_bool_mul; partial results ORed into C)
 };
 // shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
 sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape = 0);

@@ -72,6 +72,29 @@ def test_bool_mul_garbage_pad_bits_and_unaligned(w):
 
 
 @pytest.mark.parametrize("w", [32, 64])
+@pytest.mark.parametrize("shape", [(40, 3000, 90), (260, 1500, 700), (7, 9000, 33), (512, 512, 512)])
+def test_bool_mul_split_k(w, shape):
+    """Small output, long K: the product is split along K across CTAs whose partial
+    results are ORed together.  Garbage pad bits in C must come out zero, with and
+    without accumulation, exactly as in the unsplit product."""
+    R, K, N = shape
+    rng = np.random.default_rng(K)
+    A, B = rand_bool(rng, R, K, 0.01), rand_bool(rng, K, N, 0.01)
+    ref = oracle.mul(A, B, 1)
+    C0 = rand_bool(rng, R, N, 0.05)
+    Cp = packed(C0, w).copy()
+    dt = np.uint64 if w == 64 else np.uint32
+    last, nb = (N - 1) // w, N % w                   # the row's last word and its valid bits
+    if nb:
+        Cp[:, last] |= ~dt((1 << nb) - 1)
+    for acc in (False, True):
+        got = gpu_bool_mul(packed(A, w), packed(B, w), K, N, w, C0=Cp if acc else None, pad=(0, 1, 1))
+        assert np.array_equal(unpacked(got, w, N), np.maximum(C0, ref) if acc else ref)
+        if nb:
+            assert int((got[:, last] >> dt(nb)).sum()) == 0
+
+
+@pytest.mark.parametrize("w", [32, 64])
 def test_pack_unpack(w):
     import torch
     import paper_1705_08743_gb300 as sr
