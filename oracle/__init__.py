@@ -7,7 +7,8 @@ baseline may import this package; the library under
 The arithmetic lives in ``oracle.c`` (plain C, OpenMP over independent rows);
 this module compiles it with gcc on first use and wraps it for numpy arrays.
 Entries are integers in {0..S}: S = 1 is the Boolean semiring of Section 2,
-S = 255 / 65535 the anti-distance matrices of Sections 3-4.
+S = 255 / 65535 / 2^32 − 1 the anti-distance matrices of Sections 3-4 (all
+sums are formed in 64 bits, so the u32 type needs no special case).
 
 Parity status of each function is recorded in the tests that pin it
 (``tests/test_oracle_pins.py``): every function here is pinned against

@@ -22,7 +22,8 @@ import oracle
 import synth
 from golden_io import all_fixtures, load
 
-SS = [1, 255, 65535]
+S32 = 2 ** 32 - 1                    # the u32 anti-distance type (Section 4)
+SS = [1, 255, 65535, S32]
 
 
 def rand_mat(rng, R, C, S, density=0.5, lo=None):
@@ -132,6 +133,36 @@ def test_times_table_u16_sampled_by_distances():
     assert np.array_equal(S - P.astype(np.int64), np.minimum(d[:, None] + d[None, :], S))
 
 
+def test_times_table_u32_sampled_by_distances():
+    """S = 2^32 − 1: a + b − S needs 33 bits; the closed form through distances
+    (computed here in Python integers) fixes every entry, including the carry edge
+    a + b = S, S + 1 and the extremes 0 and S."""
+    S = S32
+    rng = np.random.default_rng(9)
+    a = np.concatenate([np.array([0, 1, 2, S - 1, S, 2 ** 31 - 1, 2 ** 31, 2 ** 31 + 1, 2 ** 16, 2 ** 32 - 2 ** 16]),
+                        rng.integers(0, S + 1, 300, dtype=np.int64)]).astype(np.uint32)
+    P = oracle.mul(a[:, None], a[None, :], S)
+    d = S - a.astype(np.int64)
+    assert np.array_equal(S - P.astype(np.int64), np.minimum(d[:, None] + d[None, :], S))
+    ai = [int(x) for x in a[:10]]
+    for i, x in enumerate(ai):
+        for j, y in enumerate(ai):
+            assert int(P[i, j]) == max(x + y - S, 0)
+
+
+def test_u32_closure_is_u16_closure_shifted_when_paths_are_short():
+    """With edge lengths <= 31 and D = 50 every path is shorter than 2^16 − 1, so
+    no value saturates in either type and each reachable entry is S − length:
+    the u32 closure equals the u16 one plus (2^32 − 1) − (2^16 − 1) where nonzero."""
+    rng = np.random.default_rng(13)
+    D = 50
+    W = np.where(rng.random((D, D)) < 0.08, rng.integers(1, 32, (D, D)), 0).astype(np.uint32)
+    T16 = oracle.warshall(oracle.encode_antidist(W, 65535), 65535).astype(np.int64)
+    T32 = oracle.warshall(oracle.encode_antidist(W, S32), S32).astype(np.int64)
+    assert np.array_equal(T32, np.where(T16 > 0, T16 + (S32 - 65535), 0))
+    assert (T16 > 0).sum() > D                                # the graph has long paths
+
+
 def test_times_boolean_truth_table():
     a = np.array([0, 1], np.uint32)
     P = oracle.mul(a[:, None], a[None, :], 1)
@@ -172,7 +203,7 @@ def test_closure_brute_force(S, D):
             assert np.array_equal(oracle.closure_row(A, i, S), T[i])
 
 
-@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("S", [255, 65535, S32])
 def test_closure_vs_scipy_floyd_warshall(S):
     sp = pytest.importorskip("scipy.sparse.csgraph")
     rng = np.random.default_rng(7)
@@ -236,7 +267,7 @@ def test_associativity_distributivity(S):
                           np.maximum(oracle.mul(A, B, S), oracle.mul(A2, B, S)))
 
 
-@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("S", [255, 65535, S32])
 def test_de_morgan_duality(S):
     rng = np.random.default_rng(31)
     A, B = rand_mat(rng, 11, 14, S, density=0.7), rand_mat(rng, 14, 9, S, density=0.7)
@@ -244,7 +275,7 @@ def test_de_morgan_duality(S):
     assert np.array_equal(S - oracle.mul(A, B, S).astype(np.int64), minplus_sat(nA, nB, S))
 
 
-@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("S", [255, 65535, S32])
 def test_boolean_embedding(S):
     rng = np.random.default_rng(41)
     A = rand_mat(rng, 30, 30, 1, density=0.07)
@@ -369,7 +400,7 @@ def brute_dist_closure(Dm, S):
     return T.astype(np.uint32)
 
 
-@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("S", [255, 65535, S32])
 def test_dist_mul_by_de_morgan_and_brute_force(S):
     rng = np.random.default_rng(51)
     A, B = rand_mat(rng, 9, 13, S, density=0.6), rand_mat(rng, 13, 7, S, density=0.6)
@@ -381,7 +412,7 @@ def test_dist_mul_by_de_morgan_and_brute_force(S):
     assert np.array_equal(oracle.dist_mul(dA, dB, S, Z=Z), np.minimum(Z, minplus_sat(dA, dB, S)))
 
 
-@pytest.mark.parametrize("S", [255, 65535])
+@pytest.mark.parametrize("S", [255, 65535, S32])
 @pytest.mark.parametrize("D", [1, 4, 7])
 def test_dist_closure_brute_force_and_de_morgan(S, D):
     rng = np.random.default_rng(60 + D)
