@@ -9,7 +9,7 @@ Default workload (one "step" = the whole hot path over one batch):
   the product (2·4096^3 per step), in Gop/s.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-        [--workload cfg2|cfg2-8192|cfg1|cfg3|u16] [--no-cpu] [--no-e2e]
+        [--workload cfg2|cfg2-8192|u16|u32|cfg1|cfg3|cfg4|cfg4-200|cfg5] [--no-cpu] [--no-e2e]
 Under torchrun each rank runs an independent replica on its own GPU (the
 closure does not shard without an exchange step; replicas only) and rank 0
 prints one JSON line with the max-over-ranks time.
@@ -154,7 +154,7 @@ def load_traffic(kernel_key: str, sources):
 
 
 class Cfg2:
-    """Anti-distance closure + product, D x D u8 (or u16)."""
+    """Anti-distance closure + product, D x D u8 (or u16, u32)."""
 
     def __init__(self, D=4096, dtype="u8"):
         self.D, self.dtype = D, dtype
@@ -165,7 +165,7 @@ class Cfg2:
     def host_inputs(self):
         import numpy as np
         import synth
-        npdt = np.uint8 if self.dtype == "u8" else np.uint16
+        npdt = {"u8": np.uint8, "u16": np.uint16, "u32": np.uint32}[self.dtype]
         WA = synth.cfg2_antidist(D=self.D, seed=1, s_edge=0, dtype=npdt)
         WB = synth.cfg2_antidist(D=self.D, seed=1, s_edge=3, dtype=npdt)
         return WA, WB
@@ -173,9 +173,9 @@ class Cfg2:
     def setup_device(self, WA, WB, dev):
         import torch
         import paper_1705_08743_gb300 as sr
-        tdt = torch.uint8 if self.dtype == "u8" else torch.int16
-        self.sdt = sr.SR_U8 if self.dtype == "u8" else sr.SR_U16
-        view = (lambda a: a) if self.dtype == "u8" else (lambda a: a.view("int16"))
+        tdt = {"u8": torch.uint8, "u16": torch.int16, "u32": torch.int32}[self.dtype]
+        self.sdt = {"u8": sr.SR_U8, "u16": sr.SR_U16, "u32": sr.SR_U32}[self.dtype]
+        view = self._view
         self.WA = torch.from_numpy(view(WA)).to(dev)
         self.WB = torch.from_numpy(view(WB)).to(dev)
         D = self.D
@@ -215,7 +215,7 @@ class Cfg2:
     # host-buffer path: H2D of both weight matrices, the step, D2H of T and C
     def e2e_setup(self, WA, WB):
         import torch
-        view = (lambda a: a) if self.dtype == "u8" else (lambda a: a.view("int16"))
+        view = self._view
         self.hWA = torch.from_numpy(view(WA)).pin_memory()
         self.hWB = torch.from_numpy(view(WB)).pin_memory()
         self.hT = torch.empty(self.hWA.shape, dtype=self.hWA.dtype).pin_memory()
@@ -230,15 +230,27 @@ class Cfg2:
         self.hT.copy_(self.T, non_blocking=True)
         self.hC.copy_(self.C, non_blocking=True)
 
+    def _view(self, a):
+        """numpy array -> a view torch can hold (16- and 32-bit entries as signed bit patterns)."""
+        return {"u8": a, "u16": a.view("int16"), "u32": a.view("int32")}[self.dtype]
+
     # roofline of the dominant kernel: the product kernel (also the closure's phase 3)
-    roofline_kernel = "antidist_mul_kernel<KindU8,128,128,32,8,16>"
-    roofline_sources = ["paper_1705_08743_gb300/csrc/antidist.cu", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
+    @property
+    def roofline_kernel(self):
+        return {"u8": "antidist_mul_kernel<KindU8,128,128,32,8,16>",
+                "u16": "antidist_mul_kernel<KindU16,128,128,32,8,16>",
+                "u32": "antidist32_mul_kernel<128,64,8,8,8>"}[self.dtype]
+
+    @property
+    def roofline_sources(self):
+        src = "antidist32.cu" if self.dtype == "u32" else "antidist.cu"
+        return [f"paper_1705_08743_gb300/csrc/{src}", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
 
     def cpu_sample(self, WA, WB):
         """Oracle on a bounded sample: full closure at this D, product on the first rows."""
         import numpy as np
         import oracle
-        S = 255 if self.dtype == "u8" else 65535
+        S = {"u8": 255, "u16": 65535, "u32": 2 ** 32 - 1}[self.dtype]
         D = self.D
         rows = max(1, D // 4)
         t0 = time.perf_counter()
@@ -634,6 +646,7 @@ WORKLOADS = {
     "cfg2": lambda: Cfg2(4096, "u8"),
     "cfg2-8192": lambda: Cfg2(8192, "u8"),
     "u16": lambda: Cfg2(4096, "u16"),
+    "u32": lambda: Cfg2(4096, "u32"),
     "cfg4": lambda: Cfg4(2000),
     "cfg4-200": lambda: Cfg4(200),
     "cfg5": lambda: Cfg5(),
@@ -741,7 +754,8 @@ def run_ours(args, world, rank, local):
 
     # pipe peak of the product's inner operation, measured on this GPU now
     with torch.cuda.stream(stream):
-        probe = {"u8": sr.SR_PEAK_DPX_S16X2, "u16": sr.SR_PEAK_U16_PAIR}.get(wl.dtype, sr.SR_PEAK_LOP3)
+        probe = {"u8": sr.SR_PEAK_DPX_S16X2, "u16": sr.SR_PEAK_U16_PAIR,
+                 "u32": sr.SR_PEAK_U32_PAIR}.get(wl.dtype, sr.SR_PEAK_LOP3)
         pk_ms, pk_ips, pk_ops = sr.sr_peak_probe(probe, iters=8192, blocks_per_sm=8, stream=stream.cuda_stream)
 
     pre = getattr(wl, "pre_step", lambda st: None)

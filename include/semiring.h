@@ -7,13 +7,14 @@
  *
  *   Boolean (Section 2):          entries {0,1},  a ⊕ b = max(a,b),  a ⊗ b = min(a,b)
  *   anti-distance (Sections 3-4): entries {0..S}, a ⊕ b = max(a,b),  a ⊗ b = max(a+b−S, 0)
- *                                 S = 255 (u8) or 65535 (u16); entry S − d stands
+ *                                 S = 255 (u8), 65535 (u16) or 2^32 − 1 (u32, the three
+ *                                 types of Section 4); entry S − d stands
  *                                 for distance d, 0 for "no path / distance >= S".
  *
  * Conventions shared by every call
  *  - Pointers to matrix data are DEVICE pointers owned by the caller; the
  *    library never frees them.  Matrices are row-major with a leading
- *    dimension ld >= row width, in elements (u8/u16) or in words of the
+ *    dimension ld >= row width, in elements (u8/u16/u32) or in words of the
  *    Boolean word type (32- or 64-bit).
  *  - Boolean matrices are bit-packed: entry (i, j) is bit (j mod w) of word
  *    floor(j / w) of row i (w = 32 or 64), i.e. bit (j & 7) of byte (j >> 3)
@@ -58,7 +59,10 @@ typedef enum {
     SR_BOOL_W32 = 0,   /* Boolean, 32 columns per uint32 word */
     SR_BOOL_W64 = 1,   /* Boolean, 64 columns per uint64 word */
     SR_U8 = 2,         /* anti-distance, S = 255, one uint8 per entry */
-    SR_U16 = 3         /* anti-distance, S = 65535, one uint16 per entry */
+    SR_U16 = 3,        /* anti-distance, S = 65535, one uint16 per entry */
+    SR_U32 = 4         /* anti-distance, S = 2^32 − 1, one uint32 per entry (Section 4's
+                          third type; a + b − S needs 33 bits, so ⊗ is computed as the
+                          saturating subtraction b ⊖ (S − a) = max(b, S − a) − (S − a)) */
 } sr_dtype;
 
 typedef enum {
@@ -107,7 +111,7 @@ sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 
 /* ---------------------------------------------------------------- encoding (Sections 3-4) */
 
-/* T (R×C, dtype SR_U8 or SR_U16) := anti-distance encoding of integer edge
+/* T (R×C, dtype SR_U8, SR_U16 or SR_U32) := anti-distance encoding of integer edge
  * lengths W (same element type, same shape): entry = S − w for 0 < w < S,
  * and 0 for w = 0 ("no edge") or w >= S (not distinguished from infinity,
  * Section 3).  W and T may be the same buffer. */
@@ -124,7 +128,7 @@ sr_status bool_unpack(sr_ctx *ctx, const void *M, int64_t ldm, uint8_t *dense, i
 /* ---------------------------------------------------------------- products (Section 2 formula; Section 4 listings) */
 
 /* C := (accumulate ? C : 0) ⊕ A ⊗ B with A R×K, B K×N, C R×N, anti-distance
- * (dtype SR_U8 or SR_U16).  (A ⊗ B)_ij = max over k of max(A_ik + B_kj − S, 0).
+ * (dtype SR_U8, SR_U16 or SR_U32).  (A ⊗ B)_ij = max over k of max(A_ik + B_kj − S, 0).
  * C must not overlap A or B (the aliased form is the closure).
  * R, K, N >= 1 and < 2^31. */
 sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb,
@@ -145,7 +149,7 @@ sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64
 /* ---------------------------------------------------------------- closures (Section 2 Warshall; Section 3 Floyd) */
 
 /* In place: T (D×D) := A ⊕ A⊗A ⊕ A⊗A⊗A ⊕ ... (non-reflexive closure; T_ii is
- * the best cycle through i).  Anti-distance dtype SR_U8 / SR_U16; three-phase
+ * the best cycle through i).  Anti-distance dtype SR_U8 / SR_U16 / SR_U32; three-phase
  * blocked Warshall/Floyd.  Needs no workspace. */
 sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
                            void *stream);
@@ -177,7 +181,7 @@ typedef struct {
 typedef struct sr_batch sr_batch;
 
 /* Plan a batch of n independent anti-distance closures (op SR_OP_ANTIDIST_CLOSURE,
- * one dtype for the whole batch, matrices must not overlap) for one persistent
+ * one dtype for the whole batch, SR_U8 or SR_U16 (SR_U32: SR_EINVAL), matrices must not overlap) for one persistent
  * launch (Section 2 Warshall / Section 3 Floyd on every graph).  Graphs are ordered
  * by cost, largest first; graphs with D >= the cooperative threshold are closed by
  * all CTAs of a thread-block cluster together, smaller ones one per CTA.  Allocates
@@ -209,7 +213,7 @@ sr_status sr_batched(sr_ctx *ctx, const sr_desc *d, int n, void *stream);
  * be page-locked (cudaHostAlloc, torch pin_memory); pageable buffers still work but
  * serialise the loop.  Inputs must stay valid and outputs untouched until the
  * request is done.
- *  - closures (SR_OP_ANTIDIST_CLOSURE u8/u16, SR_OP_BOOL_CLOSURE W32/W64 with
+ *  - closures (SR_OP_ANTIDIST_CLOSURE u8/u16/u32, SR_OP_BOOL_CLOSURE W32/W64 with
  *    `method`): D = R; input A (or resident rA); result written to `out`.
  *  - products (SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL): A R×K (or rA), B K×N (or rB),
  *    result R×N written to `out` (NULL: no transfer back).
@@ -230,7 +234,7 @@ typedef struct {
     size_t arena_bytes;      /* device memory budget for admitted requests and resident matrices (default 1 GiB) */
     int slots;               /* concurrent stream slots: admitted work in flight (default 4) */
     int max_pending;         /* waiting requests before sr_submit answers SR_EAGAIN (default 4096) */
-    int batch_max_d;         /* anti-distance closures with D <= this are grouped into one batched launch (512) */
+    int batch_max_d;         /* u8/u16 anti-distance closures with D <= this are grouped into one batched launch (512) */
     int batch_max_graphs;    /* graphs per grouped launch (64, at most 1024) */
     int backfill_ms;         /* later requests may overtake the head while it has waited less than this (0) */
 } sr_serve_config;
@@ -307,7 +311,7 @@ sr_status bool_closure_squaring_noalloc(void *T, int64_t ldt, int64_t D, sr_dtyp
  *                 T_ii = shortest cycle through i (the Conclusion's dransclose, minimum
  *                 loop lengths on the diagonal); computed as S − antidist_closure(S − T)
  *                 in place, no workspace.
- * dtype SR_U8 or SR_U16. */
+ * dtype SR_U8, SR_U16 or SR_U32. */
 sr_status dist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                    int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream);
 sr_status dist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
@@ -342,7 +346,8 @@ typedef enum {
     SR_PEAK_DPX_S16X2 = 0,   /* max(x + a, acc) on 16-bit lane pairs (u8 product): 2 ops/instr */
     SR_PEAK_U16_PAIR = 1,    /* max(max(x, na) + nga, acc) on lane pairs (u16): 2 ops per 2 instr */
     SR_PEAK_LOP3 = 2,        /* acc |= x & m (Boolean): 32 ops/instr */
-    SR_PEAK_IADD = 3         /* 32-bit integer add (reference) */
+    SR_PEAK_IADD = 3,        /* 32-bit integer add (reference) */
+    SR_PEAK_U32_PAIR = 4     /* max(max(x, na) + pa, acc) on one 32-bit entry (u32): 1 op per 2 instr */
 } sr_peak_op;
 sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *stream, double *ms,
                         double *instr_per_s, double *ops_per_s);

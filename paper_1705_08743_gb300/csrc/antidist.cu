@@ -1,4 +1,5 @@
-// Anti-distance semiring product and closure (u8: S = 255, u16: S = 65535).
+// Anti-distance semiring product and closure (u8: S = 255, u16: S = 65535; the u32
+// kernels, S = 2^32 − 1, are in antidist32.cu and share the closure pipeline here).
 //
 // Product (Section 2 formula, Section 3 ⊗, Section 4 listings):
 //   C := (accumulate ? C : 0) ⊕ A ⊗ B,   (A ⊗ B)_ij = max_k max(A_ik + B_kj − S, 0).
@@ -25,6 +26,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "sr_common.cuh"
@@ -516,6 +518,8 @@ sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStrea
 {
     if (a.R <= 0 || a.N <= 0)
         return SR_OK;
+    if (dt == SR_U32)
+        return launch_antidist32_mul(a, vec, s, tiles);
     if (tiles == 1)
         return dt == SR_U8 ? launch_mul_cfg<KindU8, 64, 64, 32, 4, 8>(a, vec, s)
                            : launch_mul_cfg<KindU16, 64, 64, 32, 4, 8>(a, vec, s);
@@ -528,6 +532,10 @@ sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStrea
 template <class KD, int PB>
 static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cudaStream_t s)
 {
+    if constexpr (std::is_same<KD, KindU32>::value) {
+        static_assert(PB == 128, "u32 pivot block");
+        return launch_antidist32_pivot(T, ldt, D, kb, kprev, s);
+    } else {
     using Cfg = PivotCfg<KD, PB>;
     static bool attr[kMaxDevices] = {};
     const int dev = current_device();
@@ -540,6 +548,7 @@ static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cu
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
+    }
 }
 
 // Side stream (high priority) and a per-thread pool of events for the look-ahead.
@@ -691,6 +700,8 @@ sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool
 {
     if (dt == SR_U8)
         return closure_impl<KindU8>(T, ldt, D, vec, dt, s);
+    if (dt == SR_U32)
+        return closure_impl<KindU32>(T, ldt, D, vec, dt, s);
     return closure_impl<KindU16>(T, ldt, D, vec, dt, s);
 }
 
@@ -716,9 +727,12 @@ sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ld
     if (dt == SR_U8)
         antidist_encode_kernel<uint8_t><<<blocks, 256, 0, s>>>(static_cast<const uint8_t *>(W), ldw,
                                                               static_cast<uint8_t *>(T), ldt, R, C, 255u);
-    else
+    else if (dt == SR_U16)
         antidist_encode_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(W), ldw,
                                                                static_cast<uint16_t *>(T), ldt, R, C, 65535u);
+    else
+        antidist_encode_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(W), ldw,
+                                                               static_cast<uint32_t *>(T), ldt, R, C, 0xFFFFFFFFu);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;

@@ -66,9 +66,9 @@ int device_sm_count()
 }
 
 // ------------------------------------------------------------------ checks
-static bool is_anti(sr_dtype t) { return t == SR_U8 || t == SR_U16; }
+static bool is_anti(sr_dtype t) { return t == SR_U8 || t == SR_U16 || t == SR_U32; }
 static bool is_bool(sr_dtype t) { return t == SR_BOOL_W32 || t == SR_BOOL_W64; }
-static int esize(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : t == SR_BOOL_W32 ? 4 : 8; }
+static int esize(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : (t == SR_BOOL_W32 || t == SR_U32) ? 4 : 8; }
 // row width in the dtype's own units (entries or words) for a row of n entries
 static int64_t row_units(sr_dtype t, int64_t n)
 {
@@ -229,7 +229,7 @@ sr_status antidist_encode(sr_ctx *, const void *W, int64_t ldw, void *T, int64_t
 {
     const char *fn = "antidist_encode";
     if (!is_anti(dtype))
-        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
     SR_TRY(check_dim(fn, "R", R));
     SR_TRY(check_dim(fn, "C", C));
     SR_TRY(check_mat(fn, "W", W, ldw, R, C, dtype));
@@ -272,7 +272,7 @@ sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int6
 {
     const char *fn = "antidist_mul";
     if (!is_anti(dtype))
-        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
     SR_TRY(check_dim(fn, "R", R));
     SR_TRY(check_dim(fn, "K", K));
     SR_TRY(check_dim(fn, "N", N));
@@ -347,7 +347,7 @@ sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype d
 {
     const char *fn = "antidist_closure";
     if (!is_anti(dtype))
-        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
     SR_TRY(check_dim(fn, "D", D));
     SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
     const bool vec = vec_ok(dtype, {{T, ldt}});
@@ -415,7 +415,7 @@ sr_status dist_mul(sr_ctx *c, const void *A, int64_t lda, const void *B, int64_t
 {
     const char *fn = "dist_mul";
     if (!is_anti(dtype))
-        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
     SR_TRY(check_dim(fn, "R", R));
     SR_TRY(check_dim(fn, "K", K));
     SR_TRY(check_dim(fn, "N", N));
@@ -454,7 +454,7 @@ sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype
 {
     const char *fn = "dist_closure";
     if (!is_anti(dtype))
-        return fail(SR_EINVAL, "%s: dtype must be SR_U8 or SR_U16", fn);
+        return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
     SR_TRY(check_dim(fn, "D", D));
     SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
     cudaStream_t s = S(stream);

@@ -89,6 +89,10 @@ sr_status launch_entrywise(int op, const void *A, int64_t lda, const void *B, in
         entrywise_kernel<uint16_t><<<blocks_for((int64_t)R * N), 256, 0, s>>>(
             op, static_cast<const uint16_t *>(A), lda, static_cast<const uint16_t *>(B), ldb,
             static_cast<uint16_t *>(C), ldc, R, N, 65535u);
+    else if (dt == SR_U32)
+        entrywise_kernel<uint32_t><<<blocks_for((int64_t)R * N), 256, 0, s>>>(
+            op, static_cast<const uint32_t *>(A), lda, static_cast<const uint32_t *>(B), ldb,
+            static_cast<uint32_t *>(C), ldc, R, N, 0xFFFFFFFFu);
     else {
         const int u = dt == SR_BOOL_W64 ? 2 : 1;
         const int rw = dt == SR_BOOL_W64 ? 2 * ((N + 63) / 64) : (N + 31) / 32;
@@ -107,6 +111,8 @@ sr_status launch_reflexive(void *T, int64_t ldt, int D, sr_dtype dt, cudaStream_
         reflexive_kernel<uint8_t><<<blocks_for(D), 256, 0, s>>>(static_cast<uint8_t *>(T), ldt, D, (uint8_t)255);
     else if (dt == SR_U16)
         reflexive_kernel<uint16_t><<<blocks_for(D), 256, 0, s>>>(static_cast<uint16_t *>(T), ldt, D, (uint16_t)65535);
+    else if (dt == SR_U32)
+        reflexive_kernel<uint32_t><<<blocks_for(D), 256, 0, s>>>(static_cast<uint32_t *>(T), ldt, D, 0xFFFFFFFFu);
     else
         reflexive_bits_kernel<<<blocks_for(D), 256, 0, s>>>(static_cast<uint32_t *>(T),
                                                             ldt * (dt == SR_BOOL_W64 ? 2 : 1), D);

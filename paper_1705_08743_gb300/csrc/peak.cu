@@ -8,6 +8,7 @@
 //   SR_PEAK_U16_PAIR    : acc = max(max(x, na) + nga, acc) per lane (u16 inner op, 2 instructions)
 //   SR_PEAK_LOP3        : acc |= x & m (Boolean inner op, 32 columns per instruction)
 //   SR_PEAK_IADD        : acc = acc + x (plain 32-bit integer add, reference)
+//   SR_PEAK_U32_PAIR    : acc = max(max(x, na) + pa, acc) on one 32-bit entry (u32 inner op, 2 instructions)
 
 #include <algorithm>
 
@@ -35,6 +36,8 @@ __global__ void __launch_bounds__(256) peak_kernel(int iters, uint32_t seed, uin
                     nxt[j] = __viaddmax_s16x2(x, a0, acc[j]);
                 else if (OP == SR_PEAK_U16_PAIR)
                     nxt[j] = __viaddmax_u16x2(vmax_u16x2(x, a0), a1, acc[j]);
+                else if (OP == SR_PEAK_U32_PAIR)
+                    nxt[j] = __viaddmax_u32(max(x, a0), a1, acc[j]);
                 else if (OP == SR_PEAK_LOP3)
                     nxt[j] = acc[j] | (x & acc[(j + 2) & 7]);      // one three-input LOP3
                 else
@@ -62,7 +65,7 @@ extern "C" sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *s
 {
     if (!ms || !instr_per_s || !ops_per_s)
         return fail(SR_EINVAL, "sr_peak_probe: NULL output");
-    if (op < SR_PEAK_DPX_S16X2 || op > SR_PEAK_IADD)
+    if (op < SR_PEAK_DPX_S16X2 || op > SR_PEAK_U32_PAIR)
         return fail(SR_EINVAL, "sr_peak_probe: unknown op %d", op);
     if (iters <= 0 || blocks_per_sm <= 0 || blocks_per_sm > 64)
         return fail(SR_EINVAL, "sr_peak_probe: iters > 0 and 1 <= blocks_per_sm <= 64");
@@ -78,6 +81,7 @@ extern "C" sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *s
         case SR_PEAK_DPX_S16X2: peak_kernel<SR_PEAK_DPX_S16X2><<<blocks, threads, 0, s>>>(n, 0x1234u, sink); break;
         case SR_PEAK_U16_PAIR: peak_kernel<SR_PEAK_U16_PAIR><<<blocks, threads, 0, s>>>(n, 0x1234u, sink); break;
         case SR_PEAK_LOP3: peak_kernel<SR_PEAK_LOP3><<<blocks, threads, 0, s>>>(n, 0x1234u, sink); break;
+        case SR_PEAK_U32_PAIR: peak_kernel<SR_PEAK_U32_PAIR><<<blocks, threads, 0, s>>>(n, 0x1234u, sink); break;
         default: peak_kernel<SR_PEAK_IADD><<<blocks, threads, 0, s>>>(n, 0x1234u, sink); break;
         }
     };
@@ -93,9 +97,9 @@ extern "C" sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *s
     cudaEventDestroy(e1);
     cudaFreeAsync(sink, s);
     SR_CUDA_CHECK(cudaStreamSynchronize(s));
-    const double instr_per_thread = (double)iters * 16 * 8 * (op == SR_PEAK_U16_PAIR ? 2 : 1);
+    const double instr_per_thread = (double)iters * 16 * 8 * ((op == SR_PEAK_U16_PAIR || op == SR_PEAK_U32_PAIR) ? 2 : 1);
     const double ops_per_instr = op == SR_PEAK_DPX_S16X2 ? 2.0 : op == SR_PEAK_U16_PAIR ? 1.0
-                               : op == SR_PEAK_LOP3 ? 32.0 : 1.0;
+                               : op == SR_PEAK_LOP3 ? 32.0 : op == SR_PEAK_U32_PAIR ? 0.5 : 1.0;
     const double total = instr_per_thread * blocks * threads;
     *ms = t;
     *instr_per_s = total / (t * 1e-3);

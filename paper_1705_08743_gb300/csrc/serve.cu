@@ -166,7 +166,7 @@ struct ServeState {
     int inflight = 0;
 };
 
-static int es_of(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : t == SR_BOOL_W32 ? 4 : 8; }
+static int es_of(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : (t == SR_BOOL_W32 || t == SR_U32) ? 4 : 8; }
 static int64_t units_of(sr_dtype t, int64_t n)
 {
     return t == SR_BOOL_W32 ? (n + 31) / 32 : t == SR_BOOL_W64 ? (n + 63) / 64 : n;
@@ -370,8 +370,8 @@ static bool next_job(ServeState &st, Job &job)
     if (pick < 0) return false;
     Req *first = st.reqs[st.pending[pick]].get();
     auto is_small = [&](const Req &q) {
-        return q.r.op == SR_OP_ANTIDIST_CLOSURE && q.r.R <= st.cfg.batch_max_d && !q.r.rA &&
-               q.r.dtype == first->r.dtype;
+        return q.r.op == SR_OP_ANTIDIST_CLOSURE && (q.r.dtype == SR_U8 || q.r.dtype == SR_U16) &&
+               q.r.R <= st.cfg.batch_max_d && !q.r.rA && q.r.dtype == first->r.dtype;
     };
     std::vector<Req *> cand;
     if (is_small(*first)) {
@@ -574,7 +574,7 @@ sr_status sr_submit(sr_ctx *c, const sr_request *r, uint64_t *ticket)
     if (!st)
         return fail(SR_EINVAL, "sr_submit: serving is not started (sr_serve_start)");
     const sr_dtype t = (sr_dtype)r->dtype;
-    const bool anti = t == SR_U8 || t == SR_U16, boo = t == SR_BOOL_W32 || t == SR_BOOL_W64;
+    const bool anti = t == SR_U8 || t == SR_U16 || t == SR_U32, boo = t == SR_BOOL_W32 || t == SR_BOOL_W64;
     const bool closure = r->op == SR_OP_ANTIDIST_CLOSURE || r->op == SR_OP_BOOL_CLOSURE;
     if (!((r->op == SR_OP_ANTIDIST_CLOSURE || r->op == SR_OP_ANTIDIST_MUL) ? anti
           : (r->op == SR_OP_BOOL_CLOSURE || r->op == SR_OP_BOOL_MUL) ? boo : false))

@@ -79,6 +79,13 @@ struct KindU16 {
     }
 };
 
+// u32 (S = 2^32 − 1): one entry per register; its kernels (antidist32.cu) carry their
+// own arithmetic.  The type only names the entry for the shared closure pipeline.
+struct KindU32 {
+    using elem = uint32_t;
+    static constexpr uint32_t S = 0xFFFFFFFFu;
+};
+
 // Pairs of u8 entries <-> one 32-bit register of two 16-bit lanes.
 __device__ __forceinline__ uint32_t u8x2_lo(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }  // bytes 0,1
 __device__ __forceinline__ uint32_t u8x2_hi(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }  // bytes 2,3

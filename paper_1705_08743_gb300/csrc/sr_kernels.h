@@ -36,6 +36,9 @@ struct MulArgs {
 //        2 = 128x128 on a persistent grid that leaves one SM free for concurrent work
 sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
 sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s);
+// u32 kernels (antidist32.cu), reached through launch_antidist_mul / launch_antidist_closure
+sr_status launch_antidist32_mul(const MulArgs &a, bool vec, cudaStream_t s, int tiles);
+sr_status launch_antidist32_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cudaStream_t s);
 sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ldt, int R, int C,
                                  sr_dtype dt, int num_sms, cudaStream_t s);
 

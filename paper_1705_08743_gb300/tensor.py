@@ -1,7 +1,8 @@
 """Shape-inferring wrappers over the C ABI for contiguous torch tensors.
 
-Anti-distance matrices are uint8 (S = 255) or uint16-valued tensors (stored as
-torch.uint16 or int16 bit patterns); Boolean matrices are int32/int64 tensors
+Anti-distance matrices are uint8 (S = 255), uint16-valued (S = 65535, stored as
+torch.uint16 or int16 bit patterns) or uint32-valued tensors (S = 2^32 − 1, stored
+as torch.uint32 or int32 bit patterns); Boolean matrices are int32/int64 tensors
 of packed words (32/64 columns per word).  Each helper reads shapes and leading
 dimensions off the tensor and calls the C function of the same role.
 """
@@ -18,7 +19,9 @@ def anti_dtype(t: torch.Tensor) -> int:
         return C.SR_U8
     if t.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
         return C.SR_U16
-    raise TypeError(f"anti-distance tensors are uint8 or 16-bit, got {t.dtype}")
+    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return C.SR_U32
+    raise TypeError(f"anti-distance tensors are uint8, 16-bit or 32-bit, got {t.dtype}")
 
 
 def bool_dtype(t: torch.Tensor) -> int:

@@ -27,4 +27,5 @@ def to_host(t, dtype, cols=None):
 
 def sr_dtype_of(npdt):
     import paper_1705_08743_gb300 as sr
-    return {np.dtype(np.uint8): sr.SR_U8, np.dtype(np.uint16): sr.SR_U16}[np.dtype(npdt)]
+    return {np.dtype(np.uint8): sr.SR_U8, np.dtype(np.uint16): sr.SR_U16,
+            np.dtype(np.uint32): sr.SR_U32}[np.dtype(npdt)]

@@ -10,7 +10,8 @@ from gpu_util import to_dev, to_host, sr_dtype_of
 
 pytestmark = pytest.mark.gpu
 
-S_OF = {np.uint8: 255, np.uint16: 65535}
+S_OF = {np.uint8: 255, np.uint16: 65535, np.uint32: 2 ** 32 - 1}
+DTS = [np.uint8, np.uint16, np.uint32]
 
 
 def rand_anti(rng, R, C, dt, density, lo=1):
@@ -43,7 +44,7 @@ def gpu_closure(A, pad=0):
     return to_host(Td, dt)[:, :D]
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (7, 13, 5), (128, 64, 128), (200, 300, 257),
                                    (129, 33, 130), (513, 77, 1000), (64, 1, 64)])
 def test_mul_random(dt, shape):
@@ -58,7 +59,7 @@ def test_mul_random(dt, shape):
         assert np.array_equal(gpu_mul(A, B, C0), oracle.mul(A, B, S, C=C0))
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 def test_mul_unaligned_leading_dims(dt):
     rng = np.random.default_rng(3)
     A, B = rand_anti(rng, 70, 45, dt, 0.6), rand_anti(rng, 45, 99, dt, 0.6)
@@ -68,7 +69,7 @@ def test_mul_unaligned_leading_dims(dt):
     assert np.array_equal(gpu_mul(A, B, C0, pad=(16, 32, 9)), oracle.mul(A, B, S, C=C0))
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 def test_mul_special_matrices(dt):
     S = S_OF[dt]
     rng = np.random.default_rng(4)
@@ -85,7 +86,23 @@ def test_mul_special_matrices(dt):
     assert np.array_equal(gpu_mul(ones, ones), oracle.mul(ones, ones, S))
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_mul_u32_carry_edge():
+    """u32: a ⊗ b = max(a + b − S, 0) with a + b up to 2^33 − 2.  Every pair of a set
+    of values around the carry edge (a + b = S, S ± 1) and the extremes, as an outer
+    product (K = 1) and summed over K = 40 with each pair once per k."""
+    S = 2 ** 32 - 1
+    rng = np.random.default_rng(12)
+    v = np.concatenate([[0, 1, 2, 2 ** 31 - 1, 2 ** 31, 2 ** 31 + 1, 2 ** 32 - 2 ** 16, 2 ** 16, S - 1, S],
+                        rng.integers(0, S + 1, 30, dtype=np.int64)]).astype(np.uint32)
+    P = gpu_mul(v[:, None].copy(), v[None, :].copy())
+    vi = v.astype(np.int64)
+    assert np.array_equal(P.astype(np.int64), np.maximum(vi[:, None] + vi[None, :] - S, 0))
+    A = np.tile(v[:, None], (1, 40))                               # row i: a_i in every k
+    B = np.stack([np.roll(v, k) for k in range(40)])               # row k: v shifted by k
+    assert np.array_equal(gpu_mul(A, B), oracle.mul(A, B, S))
+
+
+@pytest.mark.parametrize("dt", DTS)
 @pytest.mark.parametrize("D", [1, 2, 31, 33, 63, 64, 65, 127, 129, 200, 333])
 def test_closure_random(dt, D):
     rng = np.random.default_rng(D)
@@ -95,7 +112,7 @@ def test_closure_random(dt, D):
         assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 @pytest.mark.parametrize("D", [256, 257, 385, 640, 1100])
 def test_closure_many_pivot_blocks(dt, D):
     """Several 128-wide pivot blocks: exercises the look-ahead (next pivot's panels
@@ -107,14 +124,14 @@ def test_closure_many_pivot_blocks(dt, D):
         assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 def test_closure_unaligned_ld(dt):
     rng = np.random.default_rng(8)
     A = rand_anti(rng, 150, 150, dt, 0.05, S_OF[dt] - 40)
     assert np.array_equal(gpu_closure(A, pad=5), oracle.warshall(A, S_OF[dt]))
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 def test_closure_edge_cases(dt):
     S = S_OF[dt]
     D = 300
@@ -136,9 +153,9 @@ def test_closure_edge_cases(dt):
 def test_encode_matches_oracle():
     import torch
     import paper_1705_08743_gb300 as sr
-    for dt, S in [(np.uint8, 255), (np.uint16, 65535)]:
+    for dt, S in [(np.uint8, 255), (np.uint16, 65535), (np.uint32, 2 ** 32 - 1)]:
         rng = np.random.default_rng(1)
-        W = rng.integers(0, S + 1, size=(37, 101)).astype(dt)
+        W = rng.integers(0, S + 1, size=(37, 101), dtype=np.int64).astype(dt)
         W[0, :4] = [0, 1, S - 1, S]
         Wd = to_dev(W)
         Td = torch.empty_like(Wd)

@@ -97,6 +97,10 @@ def test_batch_rejects_overlap_and_mixed_dtypes():
     c = sr.closure_desc(1 << 24, 100, 100, sr.SR_U8)
     with pytest.raises(sr.SemiringError):
         sr.sr_batch_create(None, [a, c])
+    d = sr.closure_desc(1 << 24, 100, 100, sr.SR_U32)      # the batched kernel has 16-bit lanes only
+    with pytest.raises(sr.SemiringError) as e:
+        sr.sr_batch_create(None, [d])
+    assert e.value.status == sr.SR_EINVAL
 
 
 @pytest.mark.gpu

@@ -8,7 +8,8 @@ import oracle
 from gpu_util import to_dev, to_host, sr_dtype_of
 
 pytestmark = pytest.mark.gpu
-S_OF = {np.uint8: 255, np.uint16: 65535}
+S_OF = {np.uint8: 255, np.uint16: 65535, np.uint32: 2 ** 32 - 1}
+DTS = [np.uint8, np.uint16, np.uint32]
 
 
 def rand_dist(rng, R, C, dt, p=0.4):
@@ -17,7 +18,7 @@ def rand_dist(rng, R, C, dt, p=0.4):
     return np.where(rng.random((R, C)) < p, v, S).astype(dt)     # S = no edge
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (50, 70, 90), (129, 33, 257), (300, 300, 300)])
 def test_dist_mul(dt, shape):
     import paper_1705_08743_gb300 as sr
@@ -37,7 +38,7 @@ def test_dist_mul(dt, shape):
         sr.sr_destroy(ctx)
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 @pytest.mark.parametrize("D", [1, 7, 130, 300])
 def test_dist_closure(dt, D):
     import paper_1705_08743_gb300 as sr
@@ -49,13 +50,13 @@ def test_dist_closure(dt, D):
     assert np.array_equal(to_host(Td, dt), oracle.dist_closure(A, S))
 
 
-@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("dt", DTS)
 def test_entrywise_anti(dt):
     import paper_1705_08743_gb300 as sr
     S = S_OF[dt]
     rng = np.random.default_rng(4)
-    A = rng.integers(0, S + 1, size=(37, 101)).astype(dt)
-    B = rng.integers(0, S + 1, size=(37, 101)).astype(dt)
+    A = rng.integers(0, S + 1, size=(37, 101), dtype=np.int64).astype(dt)
+    B = rng.integers(0, S + 1, size=(37, 101), dtype=np.int64).astype(dt)
     for name, op in [("and", sr.SR_EW_AND), ("or", sr.SR_EW_OR), ("xor", sr.SR_EW_XOR), ("not", sr.SR_EW_NOT)]:
         Ad, Bd, Cd = to_dev(A), to_dev(B), to_dev(np.zeros_like(A))
         sr.sr_entrywise(None, op, Ad, 101, Bd, 101, Cd, 101, 37, 101, sr_dtype_of(dt))
@@ -93,11 +94,13 @@ def test_entrywise_bits_and_reflexive(w):
     assert np.array_equal(got, want)
 
 
-def test_reflexive_anti_is_identity_join():
+@pytest.mark.parametrize("dt", DTS)
+def test_reflexive_anti_is_identity_join(dt):
     import paper_1705_08743_gb300 as sr
+    S = S_OF[dt]
     rng = np.random.default_rng(6)
-    A = rng.integers(0, 256, size=(64, 64)).astype(np.uint8)
+    A = rng.integers(0, S + 1, size=(64, 64), dtype=np.int64).astype(dt)
     Td = to_dev(A)
-    sr.sr_reflexive(None, Td, 64, 64, sr.SR_U8)
-    want = np.maximum(A, (np.eye(64) * 255).astype(np.uint8))      # I ⊕ A
-    assert np.array_equal(to_host(Td, np.uint8), want)
+    sr.sr_reflexive(None, Td, 64, 64, sr_dtype_of(dt))
+    want = np.maximum(A, (np.eye(64, dtype=np.int64) * S).astype(dt))      # I ⊕ A
+    assert np.array_equal(to_host(Td, dt), want)

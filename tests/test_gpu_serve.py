@@ -25,7 +25,7 @@ def pinned(a):
 def rand_anti(rng, R, C, S, p=0.3, lo_frac=0.7):
     lo = max(1, int(S * lo_frac))
     v = rng.integers(lo, S + 1, size=(R, C), dtype=np.int64)
-    return np.where(rng.random((R, C)) < p, v, 0).astype(np.uint8 if S == 255 else np.uint16)
+    return np.where(rng.random((R, C)) < p, v, 0).astype({255: np.uint8, 65535: np.uint16}.get(S, np.uint32))
 
 
 def words(dense, w):
@@ -45,13 +45,13 @@ def build_requests(rng):
     """(kind, request fields, host inputs, expected result) for every semiring."""
     sr = _sr()
     reqs = []
-    for D in [17, 100, 300, 640]:                           # anti-distance closures (small ones batch)
-        for S, dt in [(255, sr.SR_U8), (65535, sr.SR_U16)]:
+    for D in [17, 100, 300, 640]:                           # anti-distance closures (small u8/u16 ones batch)
+        for S, dt in [(255, sr.SR_U8), (65535, sr.SR_U16), (2 ** 32 - 1, sr.SR_U32)]:
             A = rand_anti(rng, D, D, S, p=min(1.0, 4.0 / D))
             reqs.append(dict(op=sr.SR_OP_ANTIDIST_CLOSURE, dtype=dt, R=D, A=A, B=None,
                              want=oracle.warshall(A, S).astype(A.dtype), cols=D))
     for (R, K, N) in [(50, 70, 90), (256, 130, 300)]:      # anti-distance products
-        for S, dt in [(255, sr.SR_U8), (65535, sr.SR_U16)]:
+        for S, dt in [(255, sr.SR_U8), (65535, sr.SR_U16), (2 ** 32 - 1, sr.SR_U32)]:
             A, B = rand_anti(rng, R, K, S, p=0.5), rand_anti(rng, K, N, S, p=0.5)
             reqs.append(dict(op=sr.SR_OP_ANTIDIST_MUL, dtype=dt, R=R, K=K, N=N, A=A, B=B,
                              want=oracle.mul(A, B, S).astype(A.dtype), cols=N))
