@@ -9,7 +9,7 @@ Default workload (one "step" = the whole hot path over one batch):
   the product (2·4096^3 per step), in Gop/s.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-        [--workload cfg2|cfg2-8192|u16|u32|cfg1|cfg3|cfg4|cfg4-200|cfg5] [--no-cpu] [--no-e2e]
+        [--workload cfg2|cfg2-8192|u16|u32|cfg1|cfg3|prod16k|cfg4|cfg4-200|cfg5] [--no-cpu] [--no-e2e]
 Under torchrun each rank runs an independent replica on its own GPU (the
 closure does not shard without an exchange step; replicas only) and rank 0
 prints one JSON line with the max-over-ranks time.
@@ -534,7 +534,9 @@ class CfgBool:
     words, DAG (i<j, p=2/D) union random digraph (mean out-degree 1.5), seed 2; the
     step packs the dense 0/1 input and closes it by blocked Warshall; the squaring
     form (A ⊗ (I ⊕ A)^(2^14), 15 products of 16384^3 on the tensor cores) is timed
-    beside it."""
+    beside it.  prod16k: the product A ⊗ A of the config-3 graph (16384^3, 32 columns
+    per word) off the tensor cores, where the library picks the Four Russians table
+    kernel; the masked-OR and tensor-core forms are timed beside it."""
 
     only = ""
 
@@ -543,6 +545,9 @@ class CfgBool:
         self.dtype = "bits"
         if kind == "cfg1":
             self.D, self.name = 512, "bool_mul 512x512x512, Bernoulli(0.02), seed 0, 32 columns per uint32"
+        elif kind == "prod16k":
+            self.D, self.name = 16384, ("bool_mul A x A, A = the D=16384 config-3 graph (DAG p=2/D union p=1.5/D, "
+                                        "seed 2), 32 columns per uint32, word path (Four Russians)")
         else:
             self.D, self.name = 16384, ("bool_closure D=16384 bit-packed uint64: DAG (i<j, p=2/D) union random "
                                         "digraph (p=1.5/D), seed 2; pack + blocked Warshall")
@@ -559,7 +564,7 @@ class CfgBool:
         import paper_1705_08743_gb300 as sr
         self.sr = sr
         D = self.D
-        self.w = 32 if self.kind == "cfg1" else 64
+        self.w = 64 if self.kind == "cfg3" else 32
         self.dt = sr.SR_BOOL_W32 if self.w == 32 else sr.SR_BOOL_W64
         tdt = torch.int32 if self.w == 32 else torch.int64
         self.nw = D // self.w
@@ -572,6 +577,12 @@ class CfgBool:
             sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt)
             sr.bool_pack(None, self.denseB, D, self.B, self.nw, D, D, self.dt)
             self.ctx = None
+        elif self.kind == "prod16k":
+            self.A = torch.zeros_like(self.T)
+            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt)
+            self.B = self.A
+            self.ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_MUL, self.dt, D))
+            sr.sr_set_option(self.ctx, sr.SR_OPT_BOOL_TENSOR, 0)      # word path: auto picks the tables
         else:
             self.ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, self.dt, D,
                                                                           sr.SR_CLOSURE_SQUARING))
@@ -585,6 +596,8 @@ class CfgBool:
             e0.record(stream)
         if self.kind == "cfg1":
             sr.bool_mul(None, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
+        elif self.kind == "prod16k":
+            sr.bool_mul(self.ctx, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
         else:
             sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
             sr.bool_closure(None, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_WARSHALL, s)
@@ -607,6 +620,31 @@ class CfgBool:
                 ts.append(e0.elapsed_time(e1))
         return min(ts)
 
+    def forms_ms(self, stream, reps=3):
+        """The same product by each Boolean product kernel: masked OR, Four Russians,
+        tensor cores (count, then test); bits identical to the step's."""
+        import torch
+        sr, D, s = self.sr, self.D, stream.cuda_stream
+        ref = self.T.clone()
+        out = {}
+        for name, tc, m4r in [("masked_or", 0, 0), ("four_russians", 0, 2), ("tensor", 2, 0)]:
+            sr.sr_set_option(self.ctx, sr.SR_OPT_BOOL_TENSOR, tc)
+            sr.sr_set_option(self.ctx, sr.SR_OPT_BOOL_FOUR_RUSSIANS, m4r)
+            ts = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sr.bool_mul(self.ctx, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(e0.elapsed_time(e1))
+            out[name] = min(ts)
+            out[name + "_identical"] = bool(torch.equal(self.T, ref))
+        sr.sr_set_option(self.ctx, sr.SR_OPT_BOOL_TENSOR, 0)
+        sr.sr_set_option(self.ctx, sr.SR_OPT_BOOL_FOUR_RUSSIANS, 1)
+        return out
+
     def e2e_setup(self, A, B):
         import torch
         self.hA = torch.from_numpy(A).pin_memory()
@@ -624,6 +662,8 @@ class CfgBool:
             self.denseB.copy_(self.hB, non_blocking=True)
             sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt, s)
             sr.bool_pack(None, self.denseB, D, self.B, self.nw, D, D, self.dt, s)
+        elif self.kind == "prod16k":
+            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt, s)
         self.step(stream)
         self.hT.copy_(self.T, non_blocking=True)
 
@@ -633,6 +673,11 @@ class CfgBool:
         if self.kind == "cfg1":
             oracle.bool_mul_w64(oracle.pack_bits(A), oracle.pack_bits(B), self.D)
             ops, what = float(self.D) ** 3, "oracle packed product 512^3"
+        elif self.kind == "prod16k":
+            rows = 2048
+            Ap = oracle.pack_bits(A)
+            oracle.bool_mul_w64(Ap[:rows], Ap, self.D)
+            ops, what = float(rows) * self.D * self.D, f"oracle packed product, rows 0..{rows - 1} of 16384^3"
         else:
             rows = 2048
             Ap = oracle.pack_bits(A)
@@ -652,6 +697,7 @@ WORKLOADS = {
     "cfg5": lambda: Cfg5(),
     "cfg1": lambda: CfgBool("cfg1"),
     "cfg3": lambda: CfgBool("cfg3"),
+    "prod16k": lambda: CfgBool("prod16k"),
 }
 
 
@@ -828,12 +874,24 @@ def run_ours(args, world, rank, local):
         extra = {"step_us": t * 1e3}
         if wl.kind == "cfg3":
             extra["squaring_ms"] = wl.squaring_ms(stream)
+        if wl.kind == "prod16k":
+            extra["forms_ms"] = wl.forms_ms(stream)
+        kern = {"cfg1": "bool_mul_kernel<32,16,4,4,4> (split K)", "prod16k": "bool_m4r_kernel<8>",
+                "cfg3": "bool_mul_kernel<128,64,4,4,16> (closure phase 3) + bool_pivot_kernel<128>"}[wl.kind]
+        achieved = wl.ops / (t * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": pk_ops / 1e9, "unit": "Gop/s",
+                "frac": achieved / (pk_ops / 1e9),
+                "peak_source": "measured now: issue-bound LOP3 (acc | x & m, 32 columns per instruction) on all SMs"
+                               + ("; the table method needs fewer instructions per op than the masked OR"
+                                  if wl.kind == "prod16k" else ""),
+                "launch_ms": t, "traffic": None}
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bits", "data": "synthetic",
             "config": {"workload": wl.name, "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)"},
-            "boolean": extra, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}), flush=True)
+            "boolean": extra, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk}), flush=True)
         return
     if isinstance(wl, Cfg4):
         print(json.dumps(cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, launches, clk,

@@ -103,9 +103,13 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
 
 /* Options of a context. */
 typedef enum {
-    SR_OPT_BOOL_TENSOR = 1   /* Boolean products on the tensor cores (count, then test > 0):
+    SR_OPT_BOOL_TENSOR = 1,  /* Boolean products on the tensor cores (count, then test > 0):
                                 0 never, 1 when K >= 1024 (default), 2 whenever possible.
                                 Used only with enough ctx workspace (sr_workspace_query). */
+    SR_OPT_BOOL_FOUR_RUSSIANS = 2  /* Boolean products off the tensor cores by the method of
+                                Four Russians (8-bit groups of K, 256-entry OR tables of
+                                rows of B; Section 4 names the method for the product):
+                                0 never, 1 for large products (default), 2 always. */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 
@@ -141,7 +145,9 @@ sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, i
  * With a ctx whose workspace holds sr_workspace_query(SR_OP_BOOL_MUL, ..) bytes for
  * max(R, K, N), the product runs on the tensor cores as a count (fp8 0/1 operands,
  * fp32 sums, exact) followed by the test count > 0 (SR_OPT_BOOL_TENSOR); otherwise
- * on 32-bit word AND/OR. */
+ * on 32-bit words, by table lookups (Four Russians, SR_OPT_BOOL_FOUR_RUSSIANS) or by
+ * masked ORs (for each k with A_ik = 1, row k of B ORed into row i of C).  Every
+ * path gives the same bits. */
 sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb,
                    void *C, int64_t ldc, int64_t R, int64_t K, int64_t N,
                    sr_dtype dtype, int accumulate, void *stream);

@@ -189,6 +189,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->bool_tc_mode = value;
         return SR_OK;
     }
+    if (option == SR_OPT_BOOL_FOUR_RUSSIANS && value >= 0 && value <= 2) {
+        c->bool_m4r_mode = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -301,6 +305,19 @@ static bool use_tc(const sr_ctx *c, int64_t R, int64_t K, int64_t N, size_t ws_a
     return bool_tc_workspace(R, K, N) <= ws_avail && bool_tc_available();
 }
 
+// Four Russians tables pay off when its 256-row × 32-word CTAs fill the GPU about
+// 1.5 times over and K spans many 8-bit groups (GB300: 1.3x the masked-OR kernel at
+// 8192^3, 0.64x at 4096^3, where only 64 CTAs exist); smaller products keep the
+// masked-OR kernel (with split K).
+static bool use_m4r(const sr_ctx *c, int64_t R, int64_t K, int64_t ncw)
+{
+    const int mode = c ? c->bool_m4r_mode : 1;
+    if (mode == 0) return false;
+    if (mode == 2) return true;
+    const int64_t ctas = ((R + 255) / 256) * ((ncw + 31) / 32);
+    return K >= 1024 && 2 * ctas >= 3 * (int64_t)device_sm_count();
+}
+
 static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                                int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, cudaStream_t s,
                                sr_ctx *ctx = nullptr, void *ws = nullptr, size_t ws_bytes = 0)
@@ -318,6 +335,8 @@ static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_
     a.skip0w = 0x7fffffff; a.skipww = 0;
     if (use_tc(ctx, R, K, N, ws_bytes))
         return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, s);
+    if (use_m4r(ctx, R, K, a.ncw))
+        return launch_bool_mul_m4r(a, s);
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
     return launch_bool_mul(a, vec, s);
 }

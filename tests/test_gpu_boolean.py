@@ -225,3 +225,56 @@ def test_bool_mul_tensor_path(shape, w):
                 assert np.array_equal(got, want), (p, acc)
     finally:
         sr.sr_destroy(ctx)
+
+
+# ---------------------------------------------------------------- Four Russians
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 7, 33), (512, 512, 1024), (513, 300, 1030), (700, 1029, 2100),
+                                   (1100, 4100, 70), (64, 9, 4096)])
+@pytest.mark.parametrize("w", [32, 64])
+def test_bool_mul_four_russians(shape, w):
+    """Table-lookup product (8-bit groups of K) forced on for every shape: K not a
+    multiple of 8 or 32, ragged row tiles and word windows, garbage pad bits in A, B and
+    C, unaligned leading dimensions; with and without accumulation."""
+    import paper_1705_08743_gb300 as sr
+    R, K, N = shape
+    rng = np.random.default_rng(R * 17 + K * 5 + N)
+    ctx = sr.sr_create()
+    sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 0)
+    sr.sr_set_option(ctx, sr.SR_OPT_BOOL_FOUR_RUSSIANS, 2)
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    hdt = np.uint64 if w == 64 else np.uint32
+    try:
+        for p in [0.01, 0.3]:
+            A, B = rand_bool(rng, R, K, p), rand_bool(rng, K, N, p)
+            Ap, Bp = packed(A, w).copy(), packed(B, w).copy()
+            for M, n in [(Ap, K), (Bp, N)]:                    # set every pad bit
+                last, nb = (n - 1) // w, n % w
+                if nb:
+                    M[:, last] |= ~hdt((1 << nb) - 1)
+            Ad, Bd = to_dev(Ap, 1), to_dev(Bp, 3)
+            C0 = rand_bool(rng, R, N, 0.1)
+            for acc in (0, 1):
+                Cd = to_dev(packed(C0, w) if acc else np.zeros_like(packed(C0, w)), 2)
+                sr.bool_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, dt, acc)
+                out = to_host(Cd, hdt)[:, :-2]
+                want = oracle.mul(A, B, 1)
+                if acc:
+                    want = np.maximum(C0, want)
+                assert np.array_equal(unpacked(out, w, N), want), (p, acc)
+                if N % w:
+                    assert int((out[:, (N - 1) // w] >> hdt(N % w)).sum()) == 0
+    finally:
+        sr.sr_destroy(ctx)
+
+
+def test_bool_mul_four_russians_default_large():
+    """Default (auto) mode at a size where the table path is selected (8192 x 1024 x
+    8192: 256 CTAs of 256 rows x 32 words); compared with the oracle's packed product."""
+    R, K, N = 8192, 1024, 8192
+    rng = np.random.default_rng(77)
+    A, B = rand_bool(rng, R, K, 0.002), rand_bool(rng, K, N, 0.002)
+    A64, B64 = oracle.pack_bits(A), oracle.pack_bits(B)
+    got = gpu_bool_mul(A64.view(np.uint32), B64.view(np.uint32), K, N, 32)
+    want = oracle.bool_mul_w64(A64, B64, N)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want)
+    assert want.any()
