@@ -122,14 +122,21 @@ antidist_mul_kernel(MulArgs p)
     const int tiles_n = (p.N + BN - 1) / BN, tiles = tiles_n * ((p.R + BM - 1) / BM);
     const int nkt = (p.K + BK - 1) / BK;
 
-    // tiles in row-major order; a persistent grid (gridDim.x < tiles) walks them round-robin
+    // tiles in row-major order; a persistent grid (gridDim.x < tiles) walks them round-robin.
+    // skip_tile names a block of the 128x128 tile grid, which every tile shape here nests in.
+    static_assert(128 % BM == 0 && 128 % BN == 0, "tiles nest in the 128x128 grid of skip_tile");
+    const int tn128 = (p.N + 127) / 128;
+    auto skipped = [&](int t) {
+        return p.skip_tile >= 0 && ((t / tiles_n) * BM) / 128 == p.skip_tile / tn128 &&
+               ((t % tiles_n) * BN) / 128 == p.skip_tile % tn128;
+    };
     auto advance = [&](int t) {
         t += gridDim.x;
-        if (t == p.skip_tile) t += gridDim.x;
+        while (t < tiles && skipped(t)) t += gridDim.x;
         return t;
     };
     int tile = blockIdx.x;
-    if (tile == p.skip_tile) tile = advance(tile);
+    if (tile < tiles && skipped(tile)) tile = advance(tile);
 
     // ---- operand staging: global -> registers -> shared
     uint4 ra[Cfg::A_CHUNKS], rb[Cfg::B_CHUNKS];
@@ -486,13 +493,12 @@ __global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t l
 // -------------------------------------------------------------------------
 // Host launchers
 // -------------------------------------------------------------------------
+// Sets the kernel's shared-memory attribute once per device and reports how many CTAs
+// of it fit on one SM.
 template <class KD, int BM, int BN, int BK, int TM, int TN>
-static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int reserve_sms = 0)
+static sr_status mul_cfg_occupancy(bool vec, int &occ_out)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
-    const int64_t tiles = (int64_t)((a.N + BN - 1) / BN) * ((a.R + BM - 1) / BM);
-    if (tiles > 0x7fffffffLL)
-        return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
     auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
                     : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
     static int occ[2][kMaxDevices] = {};
@@ -503,9 +509,24 @@ static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int 
         SR_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Cfg::THREADS, Cfg::SMEM));
         occ[vec][dev] = n > 0 ? n : 1;
     }
+    occ_out = occ[vec][dev];
+    return SR_OK;
+}
+
+template <class KD, int BM, int BN, int BK, int TM, int TN>
+static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int reserve_sms = 0)
+{
+    using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
+    const int64_t tiles = (int64_t)((a.N + BN - 1) / BN) * ((a.R + BM - 1) / BM);
+    if (tiles > 0x7fffffffLL)
+        return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
+    auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
+                    : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
+    int occ = 1;
+    SR_TRY((mul_cfg_occupancy<KD, BM, BN, BK, TM, TN>(vec, occ)));
     int64_t grid = tiles;
     if (reserve_sms > 0) {   // persistent: leave reserve_sms SMs free for concurrent work
-        const int64_t slots = (int64_t)std::max(1, device_sm_count() - reserve_sms) * occ[vec][dev];
+        const int64_t slots = (int64_t)std::max(1, device_sm_count() - reserve_sms) * occ;
         grid = std::min(tiles, slots);
     }
     kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
@@ -523,10 +544,10 @@ sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStrea
     if (tiles == 1)
         return dt == SR_U8 ? launch_mul_cfg<KindU8, 64, 64, 32, 4, 8>(a, vec, s)
                            : launch_mul_cfg<KindU16, 64, 64, 32, 4, 8>(a, vec, s);
-    const int reserve = 0;   // hardware block scheduling balances uneven tile counts best
-    if (dt == SR_U8)
-        return launch_mul_cfg<KindU8, 128, 128, 32, 8, 16>(a, vec, s, reserve);
-    return launch_mul_cfg<KindU16, 128, 128, 32, 8, 16>(a, vec, s, reserve);
+    // hardware block scheduling balances a sparse last wave of 128x128 tiles better than
+    // splitting it into smaller tiles on a second stream (measured on GB300)
+    return dt == SR_U8 ? launch_mul_cfg<KindU8, 128, 128, 32, 8, 16>(a, vec, s)
+                       : launch_mul_cfg<KindU16, 128, 128, 32, 8, 16>(a, vec, s);
 }
 
 template <class KD, int PB>
@@ -552,19 +573,21 @@ static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cu
 }
 
 // Side stream (high priority) and a per-thread pool of events for the look-ahead.
-cudaStream_t side_stream()
+cudaStream_t side_stream(int i)
 {
-    static cudaStream_t st[kMaxDevices] = {};
+    static cudaStream_t st[kMaxDevices][kSideStreams] = {};
     static std::mutex mu;
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(mu);
-    if (!st[dev]) {
+    if (i < 0 || i >= kSideStreams)
+        return nullptr;
+    if (!st[dev][i]) {
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&st[dev], cudaStreamNonBlocking, hi) != cudaSuccess)
-            st[dev] = nullptr;
+        if (cudaStreamCreateWithPriority(&st[dev][i], cudaStreamNonBlocking, hi) != cudaSuccess)
+            st[dev][i] = nullptr;
     }
-    return st[dev];
+    return st[dev][i];
 }
 
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
@@ -643,55 +666,79 @@ static sr_status phase2(void *T, int64_t ldt, int D, int k0, int bw, bool row, s
     return launch_antidist_mul(a, dt, vec, s, 1);
 }
 
-// Pipelined three-phase blocked closure (pivot blocks of PB = 128), two streams:
-//   main  : phase 2 row panel of kb | phase 3 of kb (all blocks outside block row and
-//           column kb except the diagonal block kb+1; persistent grid leaving one SM)
-//   side  : phase 2 column panel of kb | block (kb+1, kb+1): its phase-3 update
-//           from pivot kb, then its closure (phase 1 of kb+1), on one CTA
-// so the two panel products run side by side and the serial pivot chain overlaps
-// the bulk of phase 3.  The side stream's pivot CTA reads only panel kb (final once
-// both phase-2 products are done) and writes only the diagonal block, which the
-// concurrent phase 3 skips.
+// Pipelined three-phase blocked closure with a one-block look-ahead (pivot blocks of
+// PB = 128).  The main stream runs phase 3 of pivot block kb on every block outside
+// block rows and columns kb and kb+1; meanwhile three high-priority side streams
+// prepare block kb+1:
+//   P: block (kb+1, kb+1): its update from pivot kb and its closure, on one CTA (phase 1)
+//   R: pivot kb's update of block row kb+1 (outside blocks kb, kb+1), then, once P is
+//      done, the row panel of kb+1 (phase 2)
+//   C: the same for block column kb+1
+// so phases 1 and 2 of the next block run beside phase 3 of this one instead of after
+// it.  The writers are disjoint: main writes outside rows/columns kb, kb+1; R writes
+// block row kb+1, C block column kb+1, P the diagonal block; every one of them reads
+// only panel kb, the diagonal block after P, and its own row or column.  The side work
+// for kb+1 starts once main's phase 3 of kb-1 (the last writer of block row and column
+// kb+1) and the panels of kb are done; main's phase 3 of kb+1 waits for both panels.
 template <class KD>
 static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s)
 {
     constexpr int PB = 128;
+    constexpr int NONE = 0x7fffffff;
     const int nb = (D + PB - 1) / PB;
+    auto width = [&](int kb) { return std::min(PB, D - kb * PB); };
     SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, s)));
     if (nb == 1)
         return SR_OK;
-    cudaStream_t s2 = side_stream();
-    std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
-    for (int kb = 0; kb < nb; ++kb) {
-        const int k0 = kb * PB, bw = std::min(PB, D - k0);
-        const bool next = kb + 1 < nb;
-        if (!s2) {   // single stream: phase 2, phase 3, next pivot
+    cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
+    if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
+        for (int kb = 0; kb < nb; ++kb) {
+            const int k0 = kb * PB, bw = width(kb);
             SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
             SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s));
             SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
-            if (next) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, s)));
-            continue;
+            if (kb + 1 < nb) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, s)));
         }
-        cudaEvent_t *e = ev->data() + 4 * kb;
-        SR_CUDA_CHECK(cudaEventRecord(e[0], s));                 // pivot kb closed (main order)
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
-        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s2));
-        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
-        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));          // both panels done
-        if (!next) {
-            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
+        return SR_OK;
+    }
+    std::vector<cudaEvent_t> *ev = nullptr;
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    cudaEvent_t *main_done = ev->data();              // [kb]: main's phase 3 of kb
+    cudaEvent_t *pivot_done = main_done + nb + 1;     // [kb]: block (kb, kb) closed
+    cudaEvent_t *rowp_done = pivot_done + nb + 1;     // [kb]: row panel of kb
+    cudaEvent_t *colp_done = rowp_done + nb + 1;      // [kb]: column panel of kb
+    SR_TRY(phase2<KD>(T, ldt, D, 0, width(0), true, dt, vec, s));
+    SR_TRY(phase2<KD>(T, ldt, D, 0, width(0), false, dt, vec, s));
+    SR_CUDA_CHECK(cudaEventRecord(rowp_done[0], s));
+    SR_CUDA_CHECK(cudaEventRecord(colp_done[0], s));
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * PB, bw = width(kb);
+        const bool next = kb + 1 < nb;
+        const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;     // rows/columns left out
+        if (kb > 0) {
+            SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
+        }
+        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - ex, k0, ex, 0, D - ex, k0, ex, dt, vec, s, 0));
+        if (!next)
             break;
+        SR_CUDA_CHECK(cudaEventRecord(main_done[kb], s));
+        for (cudaStream_t x : {sp, sr_, sc}) {
+            if (kb > 0) SR_CUDA_CHECK(cudaStreamWaitEvent(x, main_done[kb - 1], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(x, rowp_done[kb], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(x, colp_done[kb], 0));
         }
-        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
-        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, s2)));
-        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
-        // block (kb+1, kb+1) is logical tile (kb, kb) once block row/column kb are removed
-        const int tiles_n = (D - bw + PB - 1) / PB;
-        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 2, kb * tiles_n + kb));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
+        const int k1 = k0 + bw;
+        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, sp)));
+        SR_CUDA_CHECK(cudaEventRecord(pivot_done[kb + 1], sp));
+        SR_TRY(phase3<KD>(T, ldt, k0, bw, k1, bwn, NONE, 0, 0, D - ex, k0, ex, dt, vec, sr_, 1));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(sr_, pivot_done[kb + 1], 0));
+        SR_TRY(phase2<KD>(T, ldt, D, k1, bwn, true, dt, vec, sr_));
+        SR_CUDA_CHECK(cudaEventRecord(rowp_done[kb + 1], sr_));
+        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - ex, k0, ex, k1, bwn, NONE, 0, dt, vec, sc, 1));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(sc, pivot_done[kb + 1], 0));
+        SR_TRY(phase2<KD>(T, ldt, D, k1, bwn, false, dt, vec, sc));
+        SR_CUDA_CHECK(cudaEventRecord(colp_done[kb + 1], sc));
     }
     return SR_OK;
 }

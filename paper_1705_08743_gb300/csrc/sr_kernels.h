@@ -14,7 +14,8 @@ constexpr int kMaxDevices = 64;
 int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
-cudaStream_t side_stream();    // per-device high-priority stream for look-ahead work (may be null)
+constexpr int kSideStreams = 3;
+cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C

@@ -86,6 +86,30 @@ def test_mul_special_matrices(dt):
     assert np.array_equal(gpu_mul(ones, ones), oracle.mul(ones, ones, S))
 
 
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_mul_more_than_one_wave(dt):
+    """24 x 24 tiles of 128: more tiles than resident CTAs, a sparse last wave, ragged
+    edges, accumulation and a padded C."""
+    rng = np.random.default_rng(31)
+    S = S_OF[dt]
+    R, K, N = 3000, 40, 2990
+    A, B = rand_anti(rng, R, K, dt, 0.5), rand_anti(rng, K, N, dt, 0.5)
+    assert np.array_equal(gpu_mul(A, B), oracle.mul(A, B, S))
+    C0 = rand_anti(rng, R, N, dt, 0.3)
+    assert np.array_equal(gpu_mul(A, B, C0, pad=(0, 0, 8)), oracle.mul(A, B, S, C=C0))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_closure_24_pivot_blocks(dt):
+    """D = 3072: 24 pivot blocks, each phase 3 more than one wave of 128x128 tiles, with
+    the look-ahead chain of the next block running beside it on the side stream."""
+    rng = np.random.default_rng(32)
+    S = S_OF[dt]
+    D = 3072
+    A = rand_anti(rng, D, D, dt, 2.0 / D, S - S // 10)
+    assert np.array_equal(gpu_closure(A), oracle.warshall(A, S))
+
+
 def test_mul_u32_carry_edge():
     """u32: a ⊗ b = max(a + b − S, 0) with a + b up to 2^33 − 2.  Every pair of a set
     of values around the carry edge (a + b = S, S ± 1) and the extremes, as an outer
