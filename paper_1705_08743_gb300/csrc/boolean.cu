@@ -460,12 +460,13 @@ static BoolArgs bool_args(const uint32_t *A, const uint32_t *B, uint32_t *C, int
     return a;
 }
 
-// Pipelined blocked Warshall on bit rows (the same schedule as the anti-distance
-// closure): per pivot block kb, phase 2 as two in-place products (row panel on the
-// main stream, column panel on a high-priority side stream; monotone OR updates make
-// the in-place read/write overlap harmless), then phase 3 on the main stream over all
-// rows and words outside block kb, leaving the next diagonal block unwritten, while
-// one CTA on the side stream gives that block its update from pivot kb and closes it.
+// Pipelined blocked Warshall on bit rows with the same one-block look-ahead as the
+// anti-distance closure: per pivot block kb (PB bits = PW words), phase 3 on the main
+// stream covers every row and word outside blocks kb and kb+1, while three
+// high-priority side streams close block (kb+1, kb+1) (one CTA, after its update from
+// pivot kb), apply pivot kb to block row kb+1 and block column kb+1, and then compute
+// the row and column panels of kb+1 (monotone OR updates make the in-place read/write
+// overlap of a panel product harmless).
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
 {
     constexpr int PB = 128, PW = PB / 32;
@@ -479,58 +480,91 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
         count_launches();
         return SR_OK;
     };
+    auto width = [&](int kb) { return std::min(PB, D - kb * PB); };
+    // words [kw, end) held by blocks kb .. kb+n-1 (the last block's words run to rw)
+    auto word_end = [&](int kb, int n) { return kb + n < nb ? (kb + n) * PW : rw; };
+    // phase 2 of block b: its row panel (rows of b, words outside b) ...
+    auto row_panel = [&](int b) {
+        const int k0 = b * PB, kw = k0 / 32, bw = width(b);
+        BoolArgs a = bool_args(T + (int64_t)k0 * ldt + kw, T + (int64_t)k0 * ldt, T + (int64_t)k0 * ldt, ldt,
+                               bw, bw, D, rw - (word_end(b, 1) - kw));
+        a.skip0w = kw;
+        a.skipww = word_end(b, 1) - kw;
+        return a;
+    };
+    // ... and its column panel (rows outside b, the words of b)
+    auto col_panel = [&](int b) {
+        const int k0 = b * PB, kw = k0 / 32, bw = width(b);
+        BoolArgs a = bool_args(T + kw, T + (int64_t)k0 * ldt + kw, T + kw, ldt, D - bw, bw, bw, (bw + 31) / 32);
+        a.skip0 = k0;
+        a.skipw = bw;
+        return a;
+    };
     SR_TRY(pivot(0, -1, s));
     if (nb == 1)
         return SR_OK;
-    cudaStream_t s2 = side_stream();
+    cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
+    if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
+        for (int kb = 0; kb < nb; ++kb) {
+            const int k0 = kb * PB, bw = width(kb), kw = k0 / 32, wn = word_end(kb, 1) - kw;
+            SR_TRY(launch_bool_mul(row_panel(kb), vec, s, 2));
+            SR_TRY(launch_bool_mul(col_panel(kb), vec, s, 1));
+            BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D - bw, bw, D, rw - wn);
+            p3.skip0 = k0; p3.skipw = bw; p3.skip0w = kw; p3.skipww = wn;
+            SR_TRY(launch_bool_mul(p3, vec, s));
+            if (kb + 1 < nb) SR_TRY(pivot(kb + 1, -1, s));
+        }
+        return SR_OK;
+    }
     std::vector<cudaEvent_t> *ev = nullptr;
     SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    cudaEvent_t *main_done = ev->data();
+    cudaEvent_t *pivot_done = main_done + nb + 1;
+    cudaEvent_t *rowp_done = pivot_done + nb + 1;
+    cudaEvent_t *colp_done = rowp_done + nb + 1;
+    SR_TRY(launch_bool_mul(row_panel(0), vec, s, 2));
+    SR_TRY(launch_bool_mul(col_panel(0), vec, s, 1));
+    SR_CUDA_CHECK(cudaEventRecord(rowp_done[0], s));
+    SR_CUDA_CHECK(cudaEventRecord(colp_done[0], s));
     for (int kb = 0; kb < nb; ++kb) {
-        const int k0 = kb * PB, bw = std::min(PB, D - k0), kw = k0 / 32;
-        const int bwords = (bw + 31) / 32;
+        const int k0 = kb * PB, bw = width(kb), kw = k0 / 32;
         const bool next = kb + 1 < nb;
-        // phase 2: row panel (rows of block kb, all words but its own) ...
-        BoolArgs rowp = bool_args(T + (int64_t)k0 * ldt + kw, T + (int64_t)k0 * ldt, T + (int64_t)k0 * ldt, ldt,
-                                  bw, bw, D, next ? rw - PW : kw);
-        rowp.skip0w = next ? kw : 0x7fffffff;
-        rowp.skipww = next ? PW : 0;
-        // ... and column panel (all rows but block kb, the words of block kb)
-        BoolArgs colp = bool_args(T + kw, T + (int64_t)k0 * ldt + kw, T + kw, ldt, D - bw, bw, bw, bwords);
-        colp.skip0 = k0;
-        colp.skipw = bw;
-        // phase 3: all rows but block kb, all words but those of block kb
-        BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D - bw, bw, D, next ? rw - PW : kw);
-        p3.skip0 = k0;
-        p3.skipw = bw;
-        p3.skip0w = next ? kw : 0x7fffffff;
-        p3.skipww = next ? PW : 0;
-        if (!s2) {
-            SR_TRY(launch_bool_mul(rowp, vec, s, 2));
-            SR_TRY(launch_bool_mul(colp, vec, s, 1));
-            SR_TRY(launch_bool_mul(p3, vec, s));
-            if (next) SR_TRY(pivot(kb + 1, -1, s));
-            continue;
+        const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;          // rows left out
+        const int exw = word_end(kb, next ? 2 : 1) - kw;                  // words left out
+        if (kb > 0) {
+            SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
         }
-        cudaEvent_t *e = ev->data() + 4 * kb;
-        SR_CUDA_CHECK(cudaEventRecord(e[0], s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
-        SR_TRY(launch_bool_mul(colp, vec, s2, 1));
-        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
-        SR_TRY(launch_bool_mul(rowp, vec, s, 2));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));
-        if (!next) {
-            SR_TRY(launch_bool_mul(p3, vec, s));
-            break;
-        }
-        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
-        SR_TRY(pivot(kb + 1, kb, s2));
-        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
-        // block (kb+1, kb+1) sits at logical rows [k0, k0+PB), logical words [kw, kw+PW)
-        p3.kr0 = k0; p3.krn = PB;
-        p3.kw0 = kw; p3.kwn = PW;
+        // phase 3 of kb: rows and words outside blocks kb, kb+1
+        BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D - ex, bw, D, rw - exw);
+        p3.skip0 = k0; p3.skipw = ex; p3.skip0w = kw; p3.skipww = exw;
         SR_TRY(launch_bool_mul(p3, vec, s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
+        if (!next)
+            break;
+        SR_CUDA_CHECK(cudaEventRecord(main_done[kb], s));
+        for (cudaStream_t x : {sp, sr_, sc}) {
+            if (kb > 0) SR_CUDA_CHECK(cudaStreamWaitEvent(x, main_done[kb - 1], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(x, rowp_done[kb], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(x, colp_done[kb], 0));
+        }
+        const int k1 = k0 + bw, kw1 = k1 / 32, wn1 = (bwn + 31) / 32;
+        SR_TRY(pivot(kb + 1, kb, sp));
+        SR_CUDA_CHECK(cudaEventRecord(pivot_done[kb + 1], sp));
+        // block row kb+1 from pivot kb (words outside blocks kb, kb+1), then its panel
+        BoolArgs rs = bool_args(T + (int64_t)k1 * ldt + kw, T + (int64_t)k0 * ldt, T + (int64_t)k1 * ldt, ldt,
+                                bwn, bw, D, rw - exw);
+        rs.skip0w = kw; rs.skipww = exw;
+        SR_TRY(launch_bool_mul(rs, vec, sr_, 2));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(sr_, pivot_done[kb + 1], 0));
+        SR_TRY(launch_bool_mul(row_panel(kb + 1), vec, sr_, 2));
+        SR_CUDA_CHECK(cudaEventRecord(rowp_done[kb + 1], sr_));
+        // block column kb+1 from pivot kb (rows outside blocks kb, kb+1), then its panel
+        BoolArgs cs = bool_args(T + kw, T + (int64_t)k0 * ldt + kw1, T + kw1, ldt, D - ex, bw, bwn, wn1);
+        cs.skip0 = k0; cs.skipw = ex;
+        SR_TRY(launch_bool_mul(cs, vec, sc, 1));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(sc, pivot_done[kb + 1], 0));
+        SR_TRY(launch_bool_mul(col_panel(kb + 1), vec, sc, 1));
+        SR_CUDA_CHECK(cudaEventRecord(colp_done[kb + 1], sc));
     }
     return SR_OK;
 }
