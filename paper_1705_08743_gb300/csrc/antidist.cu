@@ -343,151 +343,314 @@ antidist_mul_kernel(MulArgs p)
 }
 
 // -------------------------------------------------------------------------
-// Phase 1 of the blocked closure: close one pivot block in registers
+// Phase 1 of the blocked closure: close one pivot block on one CTA
 // -------------------------------------------------------------------------
-// One CTA of 256 threads.  Thread (r0, c0), r0, c0 in [0,16), owns rows r0 + 16 j
-// (j < TRN) and lane-pair columns c0 + 16 m (m < TCN) of the PB×PB block, so pivot
-// kk = 16 j + q lives in register row j of threads r0 == q, and in register column
-// m = j/2, half q&1, of threads c0 == 8 (j&1) + q/2: every register index is a
-// compile-time constant while the pivot loop over q stays rolled.  Pivot rows and
-// columns are exchanged through double-buffered shared rows, one barrier per pivot.
+// One CTA of 256 threads; the 128×128 block lives in shared memory as 16-bit lane
+// pairs (rows padded to 65 words, so a column of lanes falls in distinct banks),
+// loaded and stored in coalesced 16-byte chunks.  With kprev >= 0 the block first
+// receives its phase-3 update from the previous pivot block, T_kk ⊕= T_k,prev ⊗
+// T_prev,k: a 128-deep product, thread (r0, c0), r0, c0 in [0,16), holding rows
+// r0 + 16 j and lane pairs c0 + 16 m in registers.
 //
-// With kprev >= 0 the block first receives its phase-3 update from the previous
-// pivot block (T_kk ⊕= T_k,prev ⊗ T_prev,k), so that update can run here, off the
-// critical path of the main stream.
+// The closure itself is the three-phase blocked scheme once more, on 32×32
+// sub-blocks.  For each sub-block s:
+//   1. one warp closes the diagonal sub-block D: lane = row, the 16 lane pairs of a
+//      row in registers, the pivot row shuffled from its lane (32 steps, no barrier);
+//   2. the column panel (rows outside s, columns of s) becomes x ⊗ (I ⊕ D) row by
+//      row in registers (threads 0-95), while threads 128-255 update the row panel
+//      (rows of s, columns outside s) in place: X_rj ⊕= D_rk ⊗ X_kj;
+//   3. every entry outside row and column s: X_ij ⊕= X_ik ⊗ X_kj over k in s.
+// Three barriers per sub-block instead of one per pivot.  Entries outside the block
+// width bw are zero and stay zero (0 ⊗ x = 0), so ragged blocks need no special case.
+// The in-place row panel may read entries other threads already updated; any mix of
+// old and new values gives the same result because D is closed and ⊗ is monotone.
 template <class KD, int PB>
 struct PivotCfg {
     static constexpr int TRN = PB / 16, TCN = PB / 32;
-    static constexpr size_t SMEM = (size_t)KD::AW * PB * PB * 4   // sAt: [PB][PB] broadcast words
-                                   + (size_t)PB * (PB / 2) * 4    // sBp: [PB][PB/2] lane pairs
-                                   + 2 * (PB / 2) * 4             // rowbuf[2][PB/2]
-                                   + 2 * PB * 2;                  // colbuf[2][PB] (u16)
-    static_assert(PB % 32 == 0 && PB >= 32, "pivot block");
+    static constexpr int SB = 32, NP = PB / 2, LDX = NP + 1;         // lane pairs per row, padded
+    static constexpr size_t SX = (size_t)PB * LDX * 4;                // the block
+    static constexpr size_t KPREV = (size_t)KD::AW * PB * PB * 4      // sY: [k][row] broadcast words
+                                    + (size_t)PB * NP * 4;             // sZ: [k][lane pair]
+    static constexpr size_t CLOSE = (size_t)KD::AW * SB * PB * 4      // sA: [SB][PB] broadcast column panel
+                                    + (size_t)KD::AW * SB * SB * 4    // sD: [SB][SB] broadcast diagonal
+                                    + (size_t)SB * (SB / 2) * 4;      // sDp: [SB][SB/2] diagonal lane pairs
+    static constexpr size_t SMEM = SX + (KPREV > CLOSE ? KPREV : CLOSE);
+    static_assert(PB == 128, "four 32-wide sub-blocks");
+    static_assert(SX % 16 == 0, "16-byte aligned staging after the block");
 };
 
-template <class KD, int PB>
+// rows [i0, i0+h) × columns [j0, j0+w) of T (zero outside) -> dst[r * ldd + pair] as
+// 16-bit lane pairs, PB columns, one 16-byte chunk of a row per thread and step
+template <class E, int PB, bool VEC>
+__device__ __forceinline__ void pivot_stage(const E *T, int64_t ldt, int i0, int j0, int h, int w, uint32_t *dst,
+                                            int ldd)
+{
+    constexpr int CH = 16 / (int)sizeof(E), CPR = PB / CH;          // entries per chunk, chunks per row
+    for (int c = threadIdx.x; c < PB * CPR; c += blockDim.x) {
+        const int r = c / CPR, col = (c % CPR) * CH;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < h) {
+            const E *src = T + (int64_t)(i0 + r) * ldt + j0 + col;
+            if (VEC && col + CH <= w) {
+                v = *reinterpret_cast<const uint4 *>(src);
+            } else {
+                uint32_t q[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int t = 0; t < CH; ++t)
+                    if (col + t < w)
+                        q[(t * sizeof(E)) / 4] |= (uint32_t)src[t] << (8 * ((t * sizeof(E)) % 4));
+                v = make_uint4(q[0], q[1], q[2], q[3]);
+            }
+        }
+        uint32_t *d = dst + r * ldd + col / 2;
+        if (sizeof(E) == 1) {
+            d[0] = u8x2_lo(v.x); d[1] = u8x2_hi(v.x); d[2] = u8x2_lo(v.y); d[3] = u8x2_hi(v.y);
+            d[4] = u8x2_lo(v.z); d[5] = u8x2_hi(v.z); d[6] = u8x2_lo(v.w); d[7] = u8x2_hi(v.w);
+        } else {
+            d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+        }
+    }
+}
+
+// rows [i0, i0+h) × columns [j0, j0+w) of T (zero outside), each entry a broadcast
+// to its A-operand words: y0[col * PB + row] (and y1 for u16)
+template <class KD, int PB, bool VEC>
+__device__ __forceinline__ void pivot_stage_bcast(const typename KD::elem *T, int64_t ldt, int i0, int j0, int h,
+                                                  int w, uint32_t *y0, uint32_t *y1)
+{
+    using E = typename KD::elem;
+    constexpr int CH = 16 / (int)sizeof(E), CPR = PB / CH;
+    for (int c = threadIdx.x; c < PB * CPR; c += blockDim.x) {
+        const int r = c / CPR, col = (c % CPR) * CH;
+        uint32_t q[4] = {0u, 0u, 0u, 0u};
+        if (r < h) {
+            const E *src = T + (int64_t)(i0 + r) * ldt + j0 + col;
+            if (VEC && col + CH <= w) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(src);
+                q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < CH; ++t)
+                    if (col + t < w)
+                        q[(t * sizeof(E)) / 4] |= (uint32_t)src[t] << (8 * ((t * sizeof(E)) % 4));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            const uint32_t a = (q[(t * sizeof(E)) / 4] >> (8 * ((t * sizeof(E)) % 4))) & (sizeof(E) == 1 ? 0xFFu : 0xFFFFu);
+            uint32_t a0, a1;
+            KD::bcast(a, a0, a1);
+            y0[(col + t) * PB + r] = a0;
+            if (KD::AW == 2) y1[(col + t) * PB + r] = a1;
+        }
+    }
+}
+
+template <class KD, int PB, bool VEC>
 __global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t ldt, int D, int kb, int kprev)
 {
     using E = typename KD::elem;
     using Cfg = PivotCfg<KD, PB>;
-    constexpr int TRN = Cfg::TRN, TCN = Cfg::TCN;
+    constexpr int TRN = Cfg::TRN, TCN = Cfg::TCN, SB = Cfg::SB, LDX = Cfg::LDX, NP = Cfg::NP;
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sAt0 = smem;                                  // [PB][PB]: row kk, slot r0*TRN + j
-    uint32_t *sAt1 = smem + PB * PB;                        // second broadcast word (u16)
-    uint32_t *sBp = smem + KD::AW * PB * PB;                // [PB][PB/2]: row kk, slot c0*TCN + m
-    uint32_t *rowbuf = sBp + PB * (PB / 2);                 // [2][PB/2]
-    uint16_t *colbuf = reinterpret_cast<uint16_t *>(rowbuf + 2 * (PB / 2));  // [2][PB]
+    uint32_t *sX = smem;                                    // [PB][LDX] lane pairs
+    uint32_t *stage = smem + Cfg::SX / 4;                   // kprev operands, then closure staging
 
     E *T = static_cast<E *>(Tv);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = tid >> 4, c0 = tid & 15;
     const int k0 = kb * PB, bw = min(PB, D - k0);
 
-    auto load_block = [&](int i0, int j0, int h, int w, uint32_t (&R)[TRN][TCN]) {
-#pragma unroll
-        for (int j = 0; j < TRN; ++j)
-#pragma unroll
-            for (int m = 0; m < TCN; ++m) {
-                const int r = r0 + 16 * j, c = 2 * (c0 + 16 * m);
-                uint32_t v = 0u;
-                if (r < h) {
-                    const E *src = T + (int64_t)(i0 + r) * ldt + j0 + c;
-                    if (c < w) v = (uint32_t)src[0];
-                    if (c + 1 < w) v |= (uint32_t)src[1] << 16;
-                }
-                R[j][m] = v;
-            }
-    };
-
-    uint32_t X[TRN][TCN];
-    load_block(k0, k0, bw, bw, X);
+    pivot_stage<E, PB, VEC>(T, ldt, k0, k0, bw, bw, sX, LDX);
 
     if (kprev >= 0) {
-        // X ⊕= T[block kb rows][block kprev cols] ⊗ T[block kprev rows][block kb cols]
+        uint32_t *sY0 = stage;                              // [PB][PB]: broadcast T_k,prev at [k][row]
+        uint32_t *sY1 = stage + PB * PB;
+        uint32_t *sZ = stage + KD::AW * PB * PB;            // [PB][NP]: T_prev,k lane pairs
         const int p0 = kprev * PB, pw = min(PB, D - p0);
-        uint32_t Y[TRN][TCN];
-        load_block(k0, p0, bw, pw, Y);                      // A operand, broadcast by column
-#pragma unroll
-        for (int j = 0; j < TRN; ++j)
-#pragma unroll
-            for (int m = 0; m < TCN; ++m)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t a0, a1;
-                    KD::bcast((Y[j][m] >> (16 * h)) & 0xFFFFu, a0, a1);
-                    const int kk = 2 * (c0 + 16 * m) + h;
-                    sAt0[kk * PB + r0 * TRN + j] = a0;
-                    if (KD::AW == 2) sAt1[kk * PB + r0 * TRN + j] = a1;
-                }
-        load_block(p0, k0, pw, bw, Y);                      // B operand, lane pairs by row
-#pragma unroll
-        for (int j = 0; j < TRN; ++j)
-#pragma unroll
-            for (int m = 0; m < TCN; ++m)
-                sBp[(r0 + 16 * j) * (PB / 2) + c0 * TCN + m] = Y[j][m];
+        pivot_stage<E, PB, VEC>(T, ldt, p0, k0, pw, bw, sZ, NP);
+        pivot_stage_bcast<KD, PB, VEC>(T, ldt, k0, p0, bw, pw, sY0, sY1);
         __syncthreads();
+        uint32_t X[TRN][TCN];
+#pragma unroll
+        for (int j = 0; j < TRN; ++j)
+#pragma unroll
+            for (int m = 0; m < TCN; ++m) X[j][m] = sX[(r0 + 16 * j) * LDX + c0 + 16 * m];
         for (int kk = 0; kk < pw; ++kk) {
             uint32_t bv[TCN], a0[TRN], a1[TRN];
 #pragma unroll
-            for (int m = 0; m < TCN; ++m) bv[m] = sBp[kk * (PB / 2) + c0 * TCN + m];
+            for (int m = 0; m < TCN; ++m) bv[m] = sZ[kk * NP + c0 + 16 * m];
 #pragma unroll
             for (int j = 0; j < TRN; ++j) {
-                a0[j] = sAt0[kk * PB + r0 * TRN + j];
-                a1[j] = KD::AW == 2 ? sAt1[kk * PB + r0 * TRN + j] : 0u;
+                a0[j] = sY0[kk * PB + r0 + 16 * j];
+                a1[j] = KD::AW == 2 ? sY1[kk * PB + r0 + 16 * j] : 0u;
             }
 #pragma unroll
             for (int j = 0; j < TRN; ++j)
 #pragma unroll
                 for (int m = 0; m < TCN; ++m) X[j][m] = KD::op(X[j][m], bv[m], a0[j], a1[j]);
         }
+        __syncthreads();                                    // all reads of sX and the staging done
+#pragma unroll
+        for (int j = 0; j < TRN; ++j)
+#pragma unroll
+            for (int m = 0; m < TCN; ++m) sX[(r0 + 16 * j) * LDX + c0 + 16 * m] = X[j][m];
     }
+    __syncthreads();
 
-    // close the block: pivots kk = 0 .. bw-1
+    uint32_t *sA0 = stage;                                  // [SB][PB]: broadcast X_i,32s+k
+    uint32_t *sA1 = sA0 + SB * PB;
+    uint32_t *sD0 = sA0 + KD::AW * SB * PB;                 // [SB][SB]: broadcast D_r,k at [k][r]
+    uint32_t *sD1 = sD0 + SB * SB;
+    uint32_t *sDp = sD0 + KD::AW * SB * SB;                 // [SB][SB/2]: D rows as lane pairs
+
+    for (int s = 0; s < PB / SB && SB * s < bw; ++s) {
+        const int rs = SB * s, ps = (SB / 2) * s;           // first row / lane pair of sub-block s
+        // 1. close the diagonal sub-block (one warp)
+        if (warp == 0) {
+            uint32_t d[16];
 #pragma unroll
-    for (int j = 0; j < TRN; ++j) {
-        for (int q = 0; q < 16; ++q) {
-            const int kk = 16 * j + q;
-            if (kk >= bw)
-                break;
-            const int par = kk & 1;
-            if (r0 == q) {
+            for (int p = 0; p < 16; ++p) d[p] = sX[(rs + lane) * LDX + ps + p];
 #pragma unroll
-                for (int m = 0; m < TCN; ++m)
-                    rowbuf[par * (PB / 2) + c0 * TCN + m] = X[j][m];
-            }
-            if (c0 == 8 * (j & 1) + (q >> 1)) {
-                const int sh = 16 * (q & 1);
+            for (int kk = 0; kk < SB; ++kk) {
+                uint32_t piv[16];
 #pragma unroll
-                for (int jj = 0; jj < TRN; ++jj)
-                    colbuf[par * PB + r0 * TRN + jj] = (uint16_t)(X[jj][j >> 1] >> sh);
-            }
-            __syncthreads();
-            uint32_t bv[TCN];
-#pragma unroll
-            for (int m = 0; m < TCN; ++m)
-                bv[m] = rowbuf[par * (PB / 2) + c0 * TCN + m];
-#pragma unroll
-            for (int jj = 0; jj < TRN; ++jj) {
+                for (int p = 0; p < 16; ++p) piv[p] = __shfl_sync(0xffffffffu, d[p], kk);
                 uint32_t a0, a1;
-                KD::bcast(colbuf[par * PB + r0 * TRN + jj], a0, a1);
+                KD::bcast((d[kk >> 1] >> (16 * (kk & 1))) & 0xFFFFu, a0, a1);
 #pragma unroll
-                for (int m = 0; m < TCN; ++m)
-                    X[jj][m] = KD::op(X[jj][m], bv[m], a0, a1);
+                for (int p = 0; p < 16; ++p) d[p] = KD::op(d[p], piv[p], a0, a1);
+            }
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                sX[(rs + lane) * LDX + ps + p] = d[p];
+                sDp[lane * 16 + p] = d[p];
+            }
+#pragma unroll
+            for (int kk = 0; kk < SB; ++kk) {
+                uint32_t a0, a1;
+                KD::bcast((d[kk >> 1] >> (16 * (kk & 1))) & 0xFFFFu, a0, a1);
+                sD0[kk * SB + lane] = a0;
+                if (KD::AW == 2) sD1[kk * SB + lane] = a1;
             }
         }
+        __syncthreads();
+        // 2a. column panel, one row per thread: x := x ⊗ (I ⊕ D)
+        if (tid < PB - SB) {
+            const int i = tid < rs ? tid : tid + SB;
+            uint32_t x[16], y[16];
+#pragma unroll
+            for (int p = 0; p < 16; ++p) y[p] = x[p] = sX[i * LDX + ps + p];
+#pragma unroll
+            for (int kk = 0; kk < SB; ++kk) {
+                uint32_t a0, a1;
+                KD::bcast((x[kk >> 1] >> (16 * (kk & 1))) & 0xFFFFu, a0, a1);
+                const uint4 *drow = reinterpret_cast<const uint4 *>(sDp + kk * 16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 v = drow[q];
+                    y[4 * q] = KD::op(y[4 * q], v.x, a0, a1);
+                    y[4 * q + 1] = KD::op(y[4 * q + 1], v.y, a0, a1);
+                    y[4 * q + 2] = KD::op(y[4 * q + 2], v.z, a0, a1);
+                    y[4 * q + 3] = KD::op(y[4 * q + 3], v.w, a0, a1);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                sX[i * LDX + ps + p] = y[p];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t a0, a1;
+                    KD::bcast((y[p] >> (16 * h)) & 0xFFFFu, a0, a1);
+                    sA0[(2 * p + h) * PB + i] = a0;
+                    if (KD::AW == 2) sA1[(2 * p + h) * PB + i] = a1;
+                }
+            }
+        } else if (tid >= 128) {
+            // 2b. row panel (in place): row rs + (tid & 31), 12 lane pairs outside s
+            const int r = rs + (tid & 31), g = (tid >> 5) - 4;
+            uint32_t acc[12];
+            int pc[12];
+#pragma unroll
+            for (int u = 0; u < 12; ++u) {
+                const int jq = g + 4 * u;                   // 0..47
+                pc[u] = jq < ps ? jq : jq + SB / 2;
+                acc[u] = sX[r * LDX + pc[u]];
+            }
+            for (int kk = 0; kk < SB; ++kk) {
+                const uint32_t a0 = sD0[kk * SB + (tid & 31)];
+                const uint32_t a1 = KD::AW == 2 ? sD1[kk * SB + (tid & 31)] : 0u;
+#pragma unroll
+                for (int u = 0; u < 12; ++u)
+                    acc[u] = KD::op(acc[u], sX[(rs + kk) * LDX + pc[u]], a0, a1);
+            }
+#pragma unroll
+            for (int u = 0; u < 12; ++u) sX[r * LDX + pc[u]] = acc[u];
+        }
+        __syncthreads();
+        // 3. everything outside row and column s: 96 rows × 48 lane pairs, 6 × 3 per thread
+        {
+            const int tr = tid >> 4, tc = tid & 15;
+            int ri[6], pj[3];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const int i = tr + 16 * q;
+                ri[q] = i < rs ? i : i + SB;
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int j = tc + 16 * u;
+                pj[u] = j < ps ? j : j + SB / 2;
+            }
+            uint32_t acc[6][3];
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int u = 0; u < 3; ++u) acc[q][u] = sX[ri[q] * LDX + pj[u]];
+            for (int kk = 0; kk < SB; ++kk) {
+                uint32_t a0[6], a1[6], b[3];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    a0[q] = sA0[kk * PB + ri[q]];
+                    a1[q] = KD::AW == 2 ? sA1[kk * PB + ri[q]] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 3; ++u) b[u] = sX[(rs + kk) * LDX + pj[u]];
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) acc[q][u] = KD::op(acc[q][u], b[u], a0[q], a1[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int u = 0; u < 3; ++u) sX[ri[q] * LDX + pj[u]] = acc[q][u];
+        }
+        __syncthreads();
     }
 
+    // write back in 16-byte chunks
+    constexpr int CH = 16 / (int)sizeof(E), CPR = PB / CH;
+    for (int c = tid; c < PB * CPR; c += 256) {
+        const int r = c / CPR, col = (c % CPR) * CH;
+        if (r >= bw || col >= bw)
+            continue;
+        const uint32_t *q = sX + r * LDX + col / 2;
+        E *dst = T + (int64_t)(k0 + r) * ldt + k0 + col;
+        uint4 v;
+        if (sizeof(E) == 1)
+            v = make_uint4(pack_u8x4(q[0], q[1]), pack_u8x4(q[2], q[3]), pack_u8x4(q[4], q[5]), pack_u8x4(q[6], q[7]));
+        else
+            v = make_uint4(q[0], q[1], q[2], q[3]);
+        if (VEC && col + CH <= bw) {
+            *reinterpret_cast<uint4 *>(dst) = v;
+        } else {
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int j = 0; j < TRN; ++j)
-#pragma unroll
-        for (int m = 0; m < TCN; ++m) {
-            const int r = r0 + 16 * j, c = 2 * (c0 + 16 * m);
-            if (r < bw) {
-                E *dst = T + (int64_t)(k0 + r) * ldt + k0 + c;
-                if (c < bw) dst[0] = (E)(X[j][m] & 0xFFFFu);
-                if (c + 1 < bw) dst[1] = (E)(X[j][m] >> 16);
-            }
+            for (int t = 0; t < CH; ++t)
+                if (col + t < bw) dst[t] = (E)((w4[(t * sizeof(E)) / 4] >> (8 * ((t * sizeof(E)) % 4))) & (sizeof(E) == 1 ? 0xFFu : 0xFFFFu));
         }
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -551,7 +714,7 @@ sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStrea
 }
 
 template <class KD, int PB>
-static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cudaStream_t s)
+static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, bool vec, cudaStream_t s)
 {
     if constexpr (std::is_same<KD, KindU32>::value) {
         static_assert(PB == 128, "u32 pivot block");
@@ -561,11 +724,16 @@ static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cu
     static bool attr[kMaxDevices] = {};
     const int dev = current_device();
     if (!attr[dev]) {
-        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_pivot_kernel<KD, PB>,
+        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_pivot_kernel<KD, PB, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_pivot_kernel<KD, PB, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
         attr[dev] = true;
     }
-    antidist_pivot_kernel<KD, PB><<<1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb, kprev);
+    if (vec)
+        antidist_pivot_kernel<KD, PB, true><<<1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb, kprev);
+    else
+        antidist_pivot_kernel<KD, PB, false><<<1, 256, Cfg::SMEM, s>>>(T, ldt, D, kb, kprev);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
@@ -687,7 +855,7 @@ static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
     constexpr int NONE = 0x7fffffff;
     const int nb = (D + PB - 1) / PB;
     auto width = [&](int kb) { return std::min(PB, D - kb * PB); };
-    SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, s)));
+    SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, vec, s)));
     if (nb == 1)
         return SR_OK;
     cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
@@ -697,7 +865,7 @@ static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
             SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
             SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s));
             SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
-            if (kb + 1 < nb) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, s)));
+            if (kb + 1 < nb) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, vec, s)));
         }
         return SR_OK;
     }
@@ -729,7 +897,7 @@ static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
             SR_CUDA_CHECK(cudaStreamWaitEvent(x, colp_done[kb], 0));
         }
         const int k1 = k0 + bw;
-        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, sp)));
+        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, vec, sp)));
         SR_CUDA_CHECK(cudaEventRecord(pivot_done[kb + 1], sp));
         SR_TRY(phase3<KD>(T, ldt, k0, bw, k1, bwn, NONE, 0, 0, D - ex, k0, ex, dt, vec, sr_, 1));
         SR_CUDA_CHECK(cudaStreamWaitEvent(sr_, pivot_done[kb + 1], 0));
