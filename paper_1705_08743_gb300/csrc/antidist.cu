@@ -848,6 +848,51 @@ static sr_status phase2(void *T, int64_t ldt, int D, int k0, int bw, bool row, s
 // only panel kb, the diagonal block after P, and its own row or column.  The side work
 // for kb+1 starts once main's phase 3 of kb-1 (the last writer of block row and column
 // kb+1) and the panels of kb are done; main's phase 3 of kb+1 waits for both panels.
+// Fewer blocks than this take the plain two-stream schedule (closure_two_streams):
+// with little phase-3 work per block, the look-ahead's extra launches and events
+// cost more than the panels they hide (GB300: two streams 3% faster at D = 3072,
+// the look-ahead 6% faster at D = 4096).
+constexpr int kLookAheadMinBlocks = 28;
+
+// Two-stream schedule: per pivot block kb, the two panels of kb side by side (row panel
+// on the main stream, column panel on the side stream), then phase 3 of kb on the main
+// stream over every block outside block row and column kb except the diagonal block
+// kb+1, while one CTA on the side stream gives that block its update from pivot kb and
+// closes it (phase 1 of kb+1).
+template <class KD>
+static sr_status closure_two_streams(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s,
+                                     cudaStream_t s2)
+{
+    constexpr int PB = 128;
+    const int nb = (D + PB - 1) / PB;
+    std::vector<cudaEvent_t> *ev = nullptr;
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * PB, bw = std::min(PB, D - k0);
+        const bool next = kb + 1 < nb;
+        cudaEvent_t *e = ev->data() + 4 * kb;
+        SR_CUDA_CHECK(cudaEventRecord(e[0], s));                 // pivot kb closed (main order)
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
+        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s2));
+        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
+        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));          // both panels done
+        if (!next) {
+            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
+            break;
+        }
+        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
+        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, vec, s2)));
+        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
+        // block (kb+1, kb+1) is logical 128x128 tile (kb, kb) once block row/column kb are removed
+        const int tiles_n = (D - bw + PB - 1) / PB;
+        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0, kb * tiles_n + kb));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
+    }
+    return SR_OK;
+}
+
 template <class KD>
 static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s)
 {
@@ -858,6 +903,8 @@ static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
     SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, vec, s)));
     if (nb == 1)
         return SR_OK;
+    if (nb < kLookAheadMinBlocks && side_stream(0))
+        return closure_two_streams<KD>(T, ldt, D, vec, dt, s, side_stream(0));
     cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
     if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
         for (int kb = 0; kb < nb; ++kb) {
