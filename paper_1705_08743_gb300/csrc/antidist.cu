@@ -95,10 +95,11 @@ struct MulCfg {
     static_assert(BK % CH == 0 && BN % CH == 0, "chunking");
     static_assert(A_CHUNKS * CH * THREADS == BM * BK && B_CHUNKS * CH * THREADS == BK * BN, "chunks");
     static_assert(THREADS % 32 == 0 && BM % 32 == 0, "warps");
+    static constexpr int MIN_BLOCKS = TM * TN >= 128 ? 3 : 4;      // register cap for CTAs per SM
 };
 
 template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
-__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS)
+__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
 antidist_mul_kernel(MulArgs p)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
@@ -233,35 +234,13 @@ antidist_mul_kernel(MulArgs p)
         const int next = advance(tile);
         const int nrow0 = (next / tiles_n) * BM, ncol0 = (next % tiles_n) * BN;
 
+        // C joins the result only in the epilogue (⊕ = max is commutative), so its load,
+        // issued before the k-loop, is hidden behind the k-loop
         uint32_t acc[TM][NP];
-        if (p.accumulate) {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-            __syncthreads();
 #pragma unroll
-            for (int i = 0; i < TM; ++i) {
-                const int li = (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int g = 0; g < NP / 4; ++g) {
-                    const int lc = g * (8 * TC) + tc * 8;           // 8 entries
-                    const uint32_t *row = reinterpret_cast<const uint32_t *>(sC + li * CROW);
-                    if (sizeof(E) == 1) {
-                        const uint2 v = *reinterpret_cast<const uint2 *>(row + lc / 4);
-                        acc[i][g * 4] = u8x2_lo(v.x) + kShift8; acc[i][g * 4 + 1] = u8x2_hi(v.x) + kShift8;
-                        acc[i][g * 4 + 2] = u8x2_lo(v.y) + kShift8; acc[i][g * 4 + 3] = u8x2_hi(v.y) + kShift8;
-                    } else {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(row + lc / 2);
-                        acc[i][g * 4] = v.x; acc[i][g * 4 + 1] = v.y; acc[i][g * 4 + 2] = v.z; acc[i][g * 4 + 3] = v.w;
-                    }
-                }
-            }
-            __syncthreads();                                   // sC is free again
-            if (next < tiles) cprefetch(nrow0, ncol0);           // lands during this tile's k-loop
-        } else {
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < NP; ++j) acc[i][j] = sizeof(E) == 1 ? kShift8 : 0u;
-        }
+            for (int j = 0; j < NP; ++j) acc[i][j] = sizeof(E) == 1 ? kShift8 : 0u;
 
         sstore(0);
         __syncthreads();
@@ -304,23 +283,48 @@ antidist_mul_kernel(MulArgs p)
             __syncthreads();
         }
 
-        // ---- epilogue
+        // ---- epilogue: ⊕ with C (prefetched into sC), store
+        if (p.accumulate) {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+            __syncthreads();
+        }
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-            const int r = row0 + (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+            const int li = (i / 4) * (4 * TR) + tr * 4 + (i % 4);
+            const int r = row0 + li;
             if (r >= p.R)
                 continue;
             const int pr = remap(r, p.rskip0, p.rskipw);
 #pragma unroll
             for (int g = 0; g < NP / 4; ++g) {
-                const int c = col0 + g * (8 * TC) + tc * 8;
+                const int lc = g * (8 * TC) + tc * 8;
+                const int c = col0 + lc;
                 if (c >= p.N)
                     continue;
                 E *dst = C + (int64_t)pr * p.ldc + remap(c, p.cskip0, p.cskipw);
-                const uint32_t *q = &acc[i][g * 4];
+                uint32_t q[4];
                 if (sizeof(E) == 1) {
-                    const uint32_t w0 = pack_u8x4(q[0] - kShift8, q[1] - kShift8);
-                    const uint32_t w1 = pack_u8x4(q[2] - kShift8, q[3] - kShift8);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) q[u] = acc[i][g * 4 + u] - kShift8;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) q[u] = acc[i][g * 4 + u];
+                }
+                if (p.accumulate) {
+                    const uint32_t *crow = reinterpret_cast<const uint32_t *>(sC + li * CROW);
+                    if (sizeof(E) == 1) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(crow + lc / 4);
+                        q[0] = __vmaxu2(q[0], u8x2_lo(v.x)); q[1] = __vmaxu2(q[1], u8x2_hi(v.x));
+                        q[2] = __vmaxu2(q[2], u8x2_lo(v.y)); q[3] = __vmaxu2(q[3], u8x2_hi(v.y));
+                    } else {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(crow + lc / 2);
+                        q[0] = __vmaxu2(q[0], v.x); q[1] = __vmaxu2(q[1], v.y);
+                        q[2] = __vmaxu2(q[2], v.z); q[3] = __vmaxu2(q[3], v.w);
+                    }
+                }
+                if (sizeof(E) == 1) {
+                    const uint32_t w0 = pack_u8x4(q[0], q[1]);
+                    const uint32_t w1 = pack_u8x4(q[2], q[3]);
                     if (VEC && c + 8 <= p.N) {
                         *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
                     } else {
@@ -338,6 +342,10 @@ antidist_mul_kernel(MulArgs p)
                     }
                 }
             }
+        }
+        if (p.accumulate) {
+            __syncthreads();                                   // sC is free again
+            if (next < tiles) cprefetch(nrow0, ncol0);         // lands during the next tile's k-loop
         }
     }
 }
