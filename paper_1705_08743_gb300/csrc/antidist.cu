@@ -978,31 +978,67 @@ sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool
 // -------------------------------------------------------------------------
 // Encoding: T = S − w for 0 < w < S, else 0 (Section 3)
 // -------------------------------------------------------------------------
+// One 32-bit word of entries: S − w is the bitwise complement of w for every S here
+// (2^bits − 1), w = S encodes to 0 by itself, and w = 0 ("no edge") is masked to 0.
 template <class E>
-__global__ void antidist_encode_kernel(const E *W, int64_t ldw, E *T, int64_t ldt, int R, int C, uint32_t S)
+__device__ __forceinline__ uint32_t encode_word(uint32_t x)
 {
-    const int64_t n = (int64_t)R * C;
+    if (sizeof(E) == 1) return ~x & __vcmpne4(x, 0u);
+    if (sizeof(E) == 2) return ~x & __vcmpne2(x, 0u);
+    return x ? ~x : 0u;
+}
+
+// 16-byte chunks of a row per thread (vector loads and stores when the rows are aligned)
+template <class E, bool VEC>
+__global__ void antidist_encode_kernel(const E *W, int64_t ldw, E *T, int64_t ldt, int R, int C)
+{
+    constexpr int CH = 16 / (int)sizeof(E);
+    const int cpr = (C + CH - 1) / CH;
+    const int64_t n = (int64_t)R * cpr;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / C, c = t % C;
-        const uint32_t w = W[r * ldw + c];
-        T[r * ldt + c] = (E)((w == 0u || w >= S) ? 0u : S - w);
+        const int r = (int)(t / cpr), c = (int)(t % cpr) * CH;
+        const E *src = W + (int64_t)r * ldw + c;
+        E *dst = T + (int64_t)r * ldt + c;
+        if (VEC && c + CH <= C) {
+            uint4 v = *reinterpret_cast<const uint4 *>(src);
+            v.x = encode_word<E>(v.x); v.y = encode_word<E>(v.y);
+            v.z = encode_word<E>(v.z); v.w = encode_word<E>(v.w);
+            *reinterpret_cast<uint4 *>(dst) = v;
+        } else {
+            for (int k = 0; k < CH && c + k < C; ++k) {
+                const uint32_t w = src[k];
+                dst[k] = (E)(w == 0u ? 0u : ~w);
+            }
+        }
     }
+}
+
+template <class E>
+static void launch_encode_t(const void *W, int64_t ldw, void *T, int64_t ldt, int R, int C, int num_sms,
+                            cudaStream_t s)
+{
+    constexpr int CH = 16 / (int)sizeof(E);
+    const int64_t n = (int64_t)R * ((C + CH - 1) / CH);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8));
+    const bool vec = aligned16(W) && aligned16(T) && ((ldw * (int64_t)sizeof(E)) & 15) == 0 &&
+                     ((ldt * (int64_t)sizeof(E)) & 15) == 0;
+    auto Wt = static_cast<const E *>(W);
+    auto Tt = static_cast<E *>(T);
+    if (vec)
+        antidist_encode_kernel<E, true><<<blocks, 256, 0, s>>>(Wt, ldw, Tt, ldt, R, C);
+    else
+        antidist_encode_kernel<E, false><<<blocks, 256, 0, s>>>(Wt, ldw, Tt, ldt, R, C);
 }
 
 sr_status launch_antidist_encode(const void *W, int64_t ldw, void *T, int64_t ldt, int R, int C,
                                  sr_dtype dt, int num_sms, cudaStream_t s)
 {
-    const int64_t n = (int64_t)R * C;
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8);
     if (dt == SR_U8)
-        antidist_encode_kernel<uint8_t><<<blocks, 256, 0, s>>>(static_cast<const uint8_t *>(W), ldw,
-                                                              static_cast<uint8_t *>(T), ldt, R, C, 255u);
+        launch_encode_t<uint8_t>(W, ldw, T, ldt, R, C, num_sms, s);
     else if (dt == SR_U16)
-        antidist_encode_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(W), ldw,
-                                                               static_cast<uint16_t *>(T), ldt, R, C, 65535u);
+        launch_encode_t<uint16_t>(W, ldw, T, ldt, R, C, num_sms, s);
     else
-        antidist_encode_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(W), ldw,
-                                                               static_cast<uint32_t *>(T), ldt, R, C, 0xFFFFFFFFu);
+        launch_encode_t<uint32_t>(W, ldw, T, ldt, R, C, num_sms, s);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;

@@ -174,17 +174,30 @@ def test_closure_edge_cases(dt):
     assert np.array_equal(gpu_closure(C.T.copy()), oracle.warshall(C.T.copy(), S))
 
 
-def test_encode_matches_oracle():
-    import torch
+@pytest.mark.parametrize("dt", DTS)
+@pytest.mark.parametrize("shape", [(37, 101, 0), (40, 256, 0), (33, 100, -1), (5, 3, 13)])
+def test_encode_matches_oracle(dt, shape):
+    """Unaligned rows (scalar path), aligned rows (16-byte chunks), aligned rows with a
+    ragged tail (pad -1: leading dimension rounded up to 16 bytes plus one chunk), and
+    in place; the extremes 0, 1, S-1, S in every case."""
     import paper_1705_08743_gb300 as sr
-    for dt, S in [(np.uint8, 255), (np.uint16, 65535), (np.uint32, 2 ** 32 - 1)]:
-        rng = np.random.default_rng(1)
-        W = rng.integers(0, S + 1, size=(37, 101), dtype=np.int64).astype(dt)
-        W[0, :4] = [0, 1, S - 1, S]
-        Wd = to_dev(W)
-        Td = torch.empty_like(Wd)
-        sr.antidist_encode(None, Wd, 101, Td, 101, 37, 101, sr_dtype_of(dt))
-        assert np.array_equal(to_host(Td, dt), oracle.encode_antidist(W, S).astype(dt))
+    R, C, pad = shape
+    S = S_OF[dt]
+    if pad < 0:
+        ch = 16 // np.dtype(dt).itemsize
+        pad = (-C) % ch + ch
+    rng = np.random.default_rng(C)
+    W = rng.integers(0, S + 1, size=(R, C), dtype=np.int64).astype(dt)
+    W[0, :min(4, C)] = [0, 1, S - 1, S][:min(4, C)]
+    want = oracle.encode_antidist(W, S).astype(dt)
+    Wd, Td = to_dev(W, pad), to_dev(np.zeros_like(W), pad)
+    sr.antidist_encode(None, Wd, Wd.shape[1], Td, Td.shape[1], R, C, sr_dtype_of(dt))
+    out = to_host(Td, dt)
+    assert np.array_equal(out[:, :C], want)
+    if pad:
+        assert (out[:, C:] == 0xA5).all(), "wrote past the row width"
+    sr.antidist_encode(None, Wd, Wd.shape[1], Wd, Wd.shape[1], R, C, sr_dtype_of(dt))     # in place
+    assert np.array_equal(to_host(Wd, dt)[:, :C], want)
 
 
 # ---------------------------------------------------------------- full size
