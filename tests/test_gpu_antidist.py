@@ -235,3 +235,32 @@ def test_cfg2_product_full_4096():
     got = to_host(Cd, np.uint8)
     ref = oracle.mul(A, B, 255)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("D,dt", [(700, np.uint8), (3600, np.uint16)])
+def test_closure_captured_in_cuda_graph(D, dt):
+    """The closure's side streams fork from and join back into the caller's stream, so
+    it can be captured into a CUDA graph (two-stream schedule at D=700, look-ahead at
+    D=3600 with 29 pivot blocks) and replayed; each replay closes fresh input."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    S = S_OF[dt]
+    rng = np.random.default_rng(D)
+    A = rand_anti(rng, D, D, dt, 3.0 / D, S - S // 8)
+    want = oracle.warshall(A, S)
+    src = to_dev(A)
+    T = torch.empty_like(src)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        T.copy_(src)
+        sr.antidist_closure(None, T, D, D, sr_dtype_of(dt), s.cuda_stream)      # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        T.copy_(src)
+        sr.antidist_closure(None, T, D, D, sr_dtype_of(dt), s.cuda_stream)
+    for _ in range(2):
+        T.fill_(0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(T, dt), want)
