@@ -56,6 +56,8 @@ struct BoolCfg {
     static constexpr int TR = BM / TM, TC = BNW / TNW, THREADS = TR * TC;
     static constexpr int BKB = BKW * 32;
     static constexpr size_t SMEM = (size_t)2 * (BKW * BM + BKB * BNW) * sizeof(uint32_t);
+    // K within one k-tile (closure panels and phase 3): the second B buffer is never used
+    static constexpr size_t SMEM_ONE = (size_t)(2 * BKW * BM + BKB * BNW) * sizeof(uint32_t);
     static_assert(TM % 4 == 0 && TNW % 4 == 0, "vector groups");
     static_assert(THREADS % 32 == 0, "warps");
 };
@@ -359,7 +361,7 @@ static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
         attr[vec][dev] = true;
     }
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+    kern<<<grid, Cfg::THREADS, a.K <= Cfg::BKB ? Cfg::SMEM_ONE : Cfg::SMEM, s>>>(a);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
