@@ -289,6 +289,7 @@ class Cfg4:
         sizes, W = synth.cfg4_batched(n=self.n)
         self.sizes = sizes
         self.ops = float(sum(D ** 3 for D in sizes))
+        self.alg_bytes = float(sum(4 * D * D for D in sizes))      # read + write every u16 entry once
         # rows padded to 8 entries (16 bytes) so every graph takes the vector path
         self.lds = [D + (-D) % 8 for D in sizes]
         parts = []
@@ -879,6 +880,8 @@ def run_ours(args, world, rank, local):
         kern = {"cfg1": "bool_mul_kernel<32,16,4,4,4> (split K)", "prod16k": "bool_m4r_kernel<8>",
                 "cfg3": "bool_mul_kernel<128,64,4,4,16> (closure phase 3) + bool_pivot_kernel<128>"}[wl.kind]
         achieved = wl.ops / (t * 1e-3) / 1e9
+        if wl.kind == "cfg1":            # A, B read and C written once: 3 x 512 x 512 bits
+            extra["algorithmic_hbm_gbs"] = 3 * wl.D * wl.D / 8 / (t * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": pk_ops / 1e9, "unit": "Gop/s",
                 "frac": achieved / (pk_ops / 1e9),
                 "peak_source": "measured now: issue-bound LOP3 (acc | x & m, 32 columns per instruction) on all SMs"
@@ -927,6 +930,7 @@ def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, la
     p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
     loop_ms = wl.loop_of_single_calls_ms(stream)
     achieved = wl.ops / (ms_per_step * 1e-3) / 1e9
+    traffic = load_traffic(wl.roofline_kernel, wl.roofline_sources)
     peak = pk_ops / 1e9
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -939,7 +943,9 @@ def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, la
         "roofline": {"bound": "alu", "kernel": wl.roofline_kernel, "achieved": achieved, "peak": peak,
                      "unit": "Gop/s", "frac": achieved / peak,
                      "peak_source": "measured now: issue-bound max.u16x2 + DPX add-max stream on all SMs",
-                     "launch_ms": ms_per_step, "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources)},
+                     "launch_ms": ms_per_step, "traffic": traffic,
+                     "achieved_hbm_gbs": traffic / (ms_per_step * 1e-3) / 1e9 if traffic else None,
+                     "algorithmic_hbm_gbs": wl.alg_bytes / (ms_per_step * 1e-3) / 1e9},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
     }
 

@@ -264,3 +264,61 @@ def test_closure_captured_in_cuda_graph(D, dt):
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(to_host(T, dt), want)
+
+
+@pytest.mark.slow
+def test_cfg2_closure_8192_sampled_rows_and_idempotence():
+    """Closure D=8192 u8 (the same generator at twice the size), as the benchmark runs
+    it: rows sampled across the matrix against the oracle's single-source path search,
+    and on every entry the closure property T ⊗ T ⊕ T = T (checked with the product
+    kernel, a different kernel from the closure's phase 3 launches)."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D = 8192
+    W = synth.cfg2_antidist(D=D, seed=1)
+    Wd = to_dev(W)
+    Td = torch.empty_like(Wd)
+    sr.antidist_encode(None, Wd, D, Td, D, D, D, sr.SR_U8)
+    sr.antidist_closure(None, Td, D, D, sr.SR_U8)
+    got = to_host(Td, np.uint8)
+    A = oracle.encode_antidist(W, 255)
+    for src in [0, 1, 2047, 4096, 5555, 8191]:
+        assert np.array_equal(got[src], oracle.closure_row(A, src, 255)), src
+    Cd = Td.clone()
+    sr.antidist_mul(None, Td, D, Td.clone(), D, Cd, D, D, D, D, sr.SR_U8, 1)
+    assert torch.equal(Cd, Td)
+
+
+@pytest.mark.slow
+def test_cfg2_product_8192_sampled_entries():
+    """Product 8192^3 u8: 3000 entries sampled uniformly, each against the oracle's
+    formula evaluated for that entry alone."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D = 8192
+    A = oracle.encode_antidist(synth.cfg2_antidist(D=D, seed=1, s_edge=0), 255).astype(np.uint8)
+    B = oracle.encode_antidist(synth.cfg2_antidist(D=D, seed=1, s_edge=3), 255).astype(np.uint8)
+    Cd = torch.zeros((D, D), dtype=torch.uint8, device="cuda")
+    sr.antidist_mul(None, to_dev(A), D, to_dev(B), D, Cd, D, D, D, D, sr.SR_U8, 0)
+    got = to_host(Cd, np.uint8)
+    rng = np.random.default_rng(8192)
+    for i, j in zip(rng.integers(0, D, 3000), rng.integers(0, D, 3000)):
+        assert got[i, j] == oracle.mul_entry(A, B, int(i), int(j), 255), (i, j)
+
+
+@pytest.mark.slow
+def test_u32_closure_4096_sampled_rows():
+    """The u32 benchmark workload (D=4096, lengths 1..31, S = 2^32 - 1): sampled rows
+    against single-source path search."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D, S = 4096, 2 ** 32 - 1
+    W = synth.cfg2_antidist(D=D, seed=1, dtype=np.uint32)
+    Wd = to_dev(W)
+    Td = torch.empty_like(Wd)
+    sr.antidist_encode(None, Wd, D, Td, D, D, D, sr.SR_U32)
+    sr.antidist_closure(None, Td, D, D, sr.SR_U32)
+    got = to_host(Td, np.uint32)
+    A = oracle.encode_antidist(W, S)
+    for src in [0, 777, 4095]:
+        assert np.array_equal(got[src], oracle.closure_row(A, src, S)), src
