@@ -224,11 +224,35 @@ class Cfg2:
         self.d2h = 2 * self.hT.numel() * self.hT.element_size()
 
     def e2e_step(self, stream):
-        self.WA.copy_(self.hWA, non_blocking=True)
-        self.WB.copy_(self.hWB, non_blocking=True)
-        self.step(stream)
-        self.hT.copy_(self.T, non_blocking=True)
+        """Host buffers in and out, copies overlapped with compute the way a user of the
+        library would: WB's upload and T's download run on a copy stream while the closure
+        and the product compute on `stream`."""
+        import torch
+        import paper_1705_08743_gb300 as sr
+        D, s = self.D, stream.cuda_stream
+        if not hasattr(self, "copy_stream"):
+            self.copy_stream = torch.cuda.Stream(device=stream.device)
+            self.ev = [torch.cuda.Event() for _ in range(4)]
+        cs = self.copy_stream
+        self.ev[0].record(stream)                          # step start: buffers free
+        cs.wait_event(self.ev[0])
+        self.WA.copy_(self.hWA, non_blocking=True)         # on `stream`
+        with torch.cuda.stream(cs):
+            self.WB.copy_(self.hWB, non_blocking=True)
+            self.ev[1].record(cs)
+        sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
+        sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt, s)
+        sr.antidist_closure(None, self.T, D, D, self.sdt, s)
+        self.ev[2].record(stream)                          # T final
+        with torch.cuda.stream(cs):
+            cs.wait_event(self.ev[2])
+            self.hT.copy_(self.T, non_blocking=True)
+            self.ev[3].record(cs)
+        stream.wait_event(self.ev[1])
+        sr.antidist_encode(None, self.WB, D, self.B, D, D, D, self.sdt, s)
+        sr.antidist_mul(None, self.A, D, self.B, D, self.C, D, D, D, D, self.sdt, 0, s)
         self.hC.copy_(self.C, non_blocking=True)
+        stream.wait_event(self.ev[3])                      # the step ends when both results are home
 
     def _view(self, a):
         """numpy array -> a view torch can hold (16- and 32-bit entries as signed bit patterns)."""
