@@ -322,3 +322,43 @@ def test_u32_closure_4096_sampled_rows():
     A = oracle.encode_antidist(W, S)
     for src in [0, 777, 4095]:
         assert np.array_equal(got[src], oracle.closure_row(A, src, S)), src
+
+
+def test_closures_from_two_host_threads():
+    """Two host threads close different graphs at the same time, each on its own stream,
+    with both schedules (two streams at D=1100, look-ahead at D=3600): the side streams
+    are shared by every caller, the event pools are per thread, and every wait refers to
+    work enqueued earlier, so the calls interleave without a cycle and stay bit-exact."""
+    import threading
+    import torch
+    import paper_1705_08743_gb300 as sr
+    cases = [(1100, np.uint8, 41), (3600, np.uint8, 42), (1100, np.uint16, 43), (3600, np.uint16, 44)]
+    inputs = []
+    for D, dt, seed in cases:
+        rng = np.random.default_rng(seed)
+        S = S_OF[dt]
+        A = rand_anti(rng, D, D, dt, 3.0 / D, S - S // 8)
+        inputs.append((D, dt, A, oracle.warshall(A, S)))
+    errors = []
+
+    def worker(items):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for D, dt, A, want in items:
+                    T = to_dev(A)
+                    for _ in range(2):
+                        sr.antidist_closure(None, T, D, D, sr_dtype_of(dt), s.cuda_stream)
+                    s.synchronize()
+                    if not np.array_equal(to_host(T, dt), want):
+                        errors.append((D, dt))
+        except Exception as e:          # reported below, on the main thread
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=worker, args=(inputs[i::2],)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not any(t.is_alive() for t in th), "a worker did not finish"
+    assert not errors, errors
