@@ -196,7 +196,11 @@ sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out);
 /* Enqueue the batch on `stream`.  use_graph != 0: the counter reset and the
  * persistent kernel are captured once into a CUDA graph, replayed on every later call. */
 sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream);
-/* Tuning: cluster size (1, 2 or 4), cooperative threshold on D, CTAs per SM. */
+/* Tuning: cluster size (1, 2 or 4), cooperative threshold on D, CTAs per SM.  Cluster 0
+ * selects the grouped schedule instead of the persistent kernel: blocked Floyd with
+ * pivot blocks of 128 run on every graph at once, three launches per pivot block
+ * (phase 1, one CTA per open graph; phase 2, all panels; phase 3, all remaining
+ * blocks), captured into the same CUDA graph; the other two values are then unused. */
 sr_status sr_batch_set_tuning(sr_batch *b, int cluster, int coop_threshold, int ctas_per_sm);
 sr_status sr_batch_get_tuning(const sr_batch *b, int *cluster, int *coop_threshold, int *ctas_per_sm);
 /* Autotuner: times the candidate tunings on this batch (closures are idempotent, so

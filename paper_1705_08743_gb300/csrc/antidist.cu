@@ -98,9 +98,9 @@ struct MulCfg {
     static constexpr int MIN_BLOCKS = TM * TN >= 128 ? 3 : 4;      // register cap for CTAs per SM
 };
 
+// Tiles tile0, tile0 + stride, ... of the product p (one CTA; shared memory as sized by MulCfg).
 template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
-__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
-antidist_mul_kernel(MulArgs p)
+__device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int stride)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
     using E = typename KD::elem;
@@ -132,11 +132,11 @@ antidist_mul_kernel(MulArgs p)
                ((t % tiles_n) * BN) / 128 == p.skip_tile % tn128;
     };
     auto advance = [&](int t) {
-        t += gridDim.x;
-        while (t < tiles && skipped(t)) t += gridDim.x;
+        t += stride;
+        while (t < tiles && skipped(t)) t += stride;
         return t;
     };
-    int tile = blockIdx.x;
+    int tile = tile0;
     if (tile < tiles && skipped(tile)) tile = advance(tile);
 
     // ---- operand staging: global -> registers -> shared
@@ -350,6 +350,30 @@ antidist_mul_kernel(MulArgs p)
     }
 }
 
+template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
+antidist_mul_kernel(MulArgs p)
+{
+    mul_tiles<KD, BM, BN, BK, TM, TN, VEC>(p, blockIdx.x, gridDim.x);
+}
+
+// Many independent products in one launch (the batched closure's grouped schedule):
+// CTA b computes tile b - start[i] of product i, i the last product with start[i] <= b.
+template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
+antidist_mul_grouped_kernel(const MulArgs *args, const int *start, int n)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const MulArgs p = args[lo];
+    mul_tiles<KD, BM, BN, BK, TM, TN, VEC>(p, b - start[lo], 1 << 30);
+}
+
 // -------------------------------------------------------------------------
 // Phase 1 of the blocked closure: close one pivot block on one CTA
 // -------------------------------------------------------------------------
@@ -455,7 +479,7 @@ __device__ __forceinline__ void pivot_stage_bcast(const typename KD::elem *T, in
 }
 
 template <class KD, int PB, bool VEC>
-__global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t ldt, int D, int kb, int kprev)
+__device__ __forceinline__ void pivot_block(void *Tv, int64_t ldt, int D, int kb, int kprev)
 {
     using E = typename KD::elem;
     using Cfg = PivotCfg<KD, PB>;
@@ -661,6 +685,24 @@ __global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t l
     }
 }
 
+template <class KD, int PB, bool VEC>
+__global__ void __launch_bounds__(256) antidist_pivot_kernel(void *Tv, int64_t ldt, int D, int kb, int kprev)
+{
+    pivot_block<KD, PB, VEC>(Tv, ldt, D, kb, kprev);
+}
+
+// Pivot block kb of many graphs in one launch (the batched closure's grouped schedule):
+// CTA b closes block kb of graph active[b]; phase 3 of kb-1 has already updated it.
+template <class KD, int PB>
+__global__ void __launch_bounds__(256) antidist_pivot_grouped_kernel(const BatchGraph *graphs, const int *active, int kb)
+{
+    const BatchGraph g = graphs[active[blockIdx.x]];
+    if (g.pad)
+        pivot_block<KD, PB, true>(g.T, g.ldt, g.D, kb, -1);
+    else
+        pivot_block<KD, PB, false>(g.T, g.ldt, g.D, kb, -1);
+}
+
 // -------------------------------------------------------------------------
 // Host launchers
 // -------------------------------------------------------------------------
@@ -746,6 +788,66 @@ static sr_status launch_pivot(void *T, int64_t ldt, int D, int kb, int kprev, bo
     count_launches();
     return SR_OK;
     }
+}
+
+// ---- grouped launches (the batched closure's per-pivot-block schedule)
+template <class KD, int BM, int BN, int BK, int TM, int TN>
+static sr_status launch_grouped_cfg(const MulArgs *args, const int *start, int n, int tiles, bool vec,
+                                    cudaStream_t s)
+{
+    using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
+    auto kern = vec ? antidist_mul_grouped_kernel<KD, BM, BN, BK, TM, TN, true>
+                    : antidist_mul_grouped_kernel<KD, BM, BN, BK, TM, TN, false>;
+    static bool attr[2][kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[vec][dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        attr[vec][dev] = true;
+    }
+    kern<<<tiles, Cfg::THREADS, Cfg::SMEM, s>>>(args, start, n);
+    SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
+    return SR_OK;
+}
+
+sr_status launch_antidist_mul_grouped(const MulArgs *args, const int *start, int n, int tiles, sr_dtype dt,
+                                      bool vec, bool thin, cudaStream_t s)
+{
+    if (n <= 0 || tiles <= 0)
+        return SR_OK;
+    if (thin)
+        return dt == SR_U8 ? launch_grouped_cfg<KindU8, 64, 64, 32, 4, 8>(args, start, n, tiles, vec, s)
+                           : launch_grouped_cfg<KindU16, 64, 64, 32, 4, 8>(args, start, n, tiles, vec, s);
+    return dt == SR_U8 ? launch_grouped_cfg<KindU8, 128, 128, 32, 8, 16>(args, start, n, tiles, vec, s)
+                       : launch_grouped_cfg<KindU16, 128, 128, 32, 8, 16>(args, start, n, tiles, vec, s);
+}
+
+template <class KD>
+static sr_status launch_pivot_grouped_t(const BatchGraph *graphs, const int *active, int n, int kb, cudaStream_t s)
+{
+    constexpr int PB = 128;
+    using Cfg = PivotCfg<KD, PB>;
+    constexpr size_t SMEM = Cfg::SX + Cfg::CLOSE;          // no previous-block operands
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(antidist_pivot_grouped_kernel<KD, PB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
+        attr[dev] = true;
+    }
+    antidist_pivot_grouped_kernel<KD, PB><<<n, 256, SMEM, s>>>(graphs, active, kb);
+    SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
+    return SR_OK;
+}
+
+sr_status launch_antidist_pivot_grouped(const BatchGraph *graphs, const int *active, int n, int kb, sr_dtype dt,
+                                        cudaStream_t s)
+{
+    if (n <= 0)
+        return SR_OK;
+    return dt == SR_U8 ? launch_pivot_grouped_t<KindU8>(graphs, active, n, kb, s)
+                       : launch_pivot_grouped_t<KindU16>(graphs, active, n, kb, s);
 }
 
 // Side stream (high priority) and a per-thread pool of events for the look-ahead.

@@ -385,6 +385,14 @@ struct BatchPlan {
     BatchGraph *d_graphs = nullptr;
     BatchItem *d_items = nullptr;
     int *d_counter = nullptr;
+    // grouped schedule (tuning cluster 0): per pivot block kb of 128, the pivot blocks of
+    // every graph still open at kb, then all their panels, then all their phase-3 tiles
+    struct GroupedStep { int nactive, act_off, npan, pan_off, pan_tiles, np3, p3_off, p3_tiles; };
+    std::vector<GroupedStep> gsteps;
+    int *d_gactive = nullptr;        // graph indices, concatenated per step
+    MulArgs *d_gargs = nullptr;      // products, concatenated per step and kind
+    int *d_gstart = nullptr;         // first tile of each product within its launch
+    bool gvec = true;                // every graph 16-byte aligned
     // captured launch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -405,10 +413,11 @@ static sr_status build_items(BatchPlan &p)
             small.push_back(g);
         }
     }
-    for (size_t s = 0; s < small.size(); s += p.nc) {
+    const size_t per = (size_t)std::max(1, p.nc);         // graphs per item (cluster 0: grouped, unused)
+    for (size_t s = 0; s < small.size(); s += per) {
         BatchItem it{};
         it.coop = 0;
-        it.n = (int)std::min<size_t>(p.nc, small.size() - s);
+        it.n = (int)std::min<size_t>(per, small.size() - s);
         for (int r = 0; r < it.n; ++r) it.g[r] = small[s + r];
         items.push_back(it);
     }
@@ -478,8 +487,100 @@ sr_status launch_batched_closure_flat(sr_dtype dt, const BatchGraph *d_graphs, c
     return st;
 }
 
+// The grouped schedule's launch lists: blocked Floyd with pivot blocks of 128 run on every
+// graph at once, one launch per phase and pivot block (phase 1: one CTA per open graph;
+// phase 2: both panels of every graph, 64x64 tiles; phase 3: every other block of every
+// graph, 128x128 tiles), graphs in decreasing D so the largest start first in each launch.
+static sr_status build_grouped(BatchPlan &p)
+{
+    if (p.d_gargs || p.d_gactive)
+        return SR_OK;
+    constexpr int PB = 128;
+    const int es = p.dtype == SR_U8 ? 1 : 2;
+    int maxnb = 0;
+    for (const auto &g : p.h_graphs) maxnb = std::max(maxnb, (g.D + PB - 1) / PB);
+    std::vector<int> act, start;
+    std::vector<MulArgs> args;
+    p.gvec = true;
+    for (const auto &g : p.h_graphs) p.gvec = p.gvec && g.pad;
+    auto mk = [&](const BatchGraph &g, int64_t a_off, int64_t b_off, int64_t c_off, int R, int K, int N, int rs0,
+                  int rsw, int cs0, int csw) {
+        MulArgs a;
+        char *T = static_cast<char *>(g.T);
+        a.A = T + a_off * es; a.B = T + b_off * es; a.C = T + c_off * es;
+        a.lda = a.ldb = a.ldc = g.ldt;
+        a.R = R; a.K = K; a.N = N;
+        a.accumulate = 1;
+        a.rskip0 = rs0; a.rskipw = rsw; a.cskip0 = cs0; a.cskipw = csw;
+        a.skip_tile = -1;
+        return a;
+    };
+    constexpr int NONE = 0x7fffffff;
+    int64_t total_tiles_max = 0;
+    for (int kb = 0; kb < maxnb; ++kb) {
+        BatchPlan::GroupedStep st{};
+        st.act_off = (int)act.size();
+        for (int gi : p.order)
+            if ((p.h_graphs[gi].D + PB - 1) / PB > kb) act.push_back(gi);
+        st.nactive = (int)act.size() - st.act_off;
+        for (int kind = 0; kind < 2; ++kind) {            // 0: panels (64x64 tiles), 1: phase 3 (128x128)
+            const int off = (int)args.size(), tile = kind == 0 ? 64 : 128;
+            int64_t tiles = 0;
+            auto add = [&](const MulArgs &a) {
+                start.push_back((int)tiles);
+                args.push_back(a);
+                tiles += (int64_t)((a.R + tile - 1) / tile) * ((a.N + tile - 1) / tile);
+            };
+            for (int i = st.act_off; i < st.act_off + st.nactive; ++i) {
+                const BatchGraph &g = p.h_graphs[act[i]];
+                const int D = g.D, k0 = kb * PB, bw = std::min(PB, D - k0);
+                const int64_t ld = g.ldt;
+                if (D - bw <= 0) continue;                    // a single-block graph: phase 1 only
+                if (kind == 0) {
+                    add(mk(g, k0 * ld + k0, k0 * ld, k0 * ld, bw, bw, D - bw, NONE, 0, k0, bw));   // row panel
+                    add(mk(g, k0, k0 * ld + k0, k0, D - bw, bw, bw, k0, bw, NONE, 0));             // column panel
+                } else {
+                    add(mk(g, k0, k0 * ld, 0, D - bw, bw, D - bw, k0, bw, k0, bw));                // the rest
+                }
+            }
+            if (tiles > 0x7fffffffLL)
+                return fail(SR_EINVAL, "sr_batch: too many tiles in one grouped launch");
+            total_tiles_max = std::max(total_tiles_max, tiles);
+            if (kind == 0) { st.pan_off = off; st.npan = (int)args.size() - off; st.pan_tiles = (int)tiles; }
+            else { st.p3_off = off; st.np3 = (int)args.size() - off; st.p3_tiles = (int)tiles; }
+        }
+        p.gsteps.push_back(st);
+    }
+    SR_CUDA_CHECK(cudaMalloc(&p.d_gactive, sizeof(int) * std::max<size_t>(1, act.size())));
+    SR_CUDA_CHECK(cudaMalloc(&p.d_gargs, sizeof(MulArgs) * std::max<size_t>(1, args.size())));
+    SR_CUDA_CHECK(cudaMalloc(&p.d_gstart, sizeof(int) * std::max<size_t>(1, start.size())));
+    if (!act.empty())
+        SR_CUDA_CHECK(cudaMemcpy(p.d_gactive, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice));
+    if (!args.empty()) {
+        SR_CUDA_CHECK(cudaMemcpy(p.d_gargs, args.data(), sizeof(MulArgs) * args.size(), cudaMemcpyHostToDevice));
+        SR_CUDA_CHECK(cudaMemcpy(p.d_gstart, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+    }
+    return SR_OK;
+}
+
+static sr_status enqueue_grouped(BatchPlan &p, cudaStream_t s)
+{
+    SR_TRY(build_grouped(p));
+    for (int kb = 0; kb < (int)p.gsteps.size(); ++kb) {
+        const BatchPlan::GroupedStep &st = p.gsteps[kb];
+        SR_TRY(launch_antidist_pivot_grouped(p.d_graphs, p.d_gactive + st.act_off, st.nactive, kb, p.dtype, s));
+        SR_TRY(launch_antidist_mul_grouped(p.d_gargs + st.pan_off, p.d_gstart + st.pan_off, st.npan, st.pan_tiles,
+                                           p.dtype, p.gvec, true, s));
+        SR_TRY(launch_antidist_mul_grouped(p.d_gargs + st.p3_off, p.d_gstart + st.p3_off, st.np3, st.p3_tiles,
+                                           p.dtype, p.gvec, false, s));
+    }
+    return SR_OK;
+}
+
 static sr_status enqueue_batch(BatchPlan &p, cudaStream_t s)
 {
+    if (p.nc == 0)
+        return enqueue_grouped(p, s);
     SR_CUDA_CHECK(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
     const bool u8 = p.dtype == SR_U8;
     switch (p.nc) {
@@ -569,14 +670,18 @@ sr_status sr_batch_set_tuning(sr_batch *b, int cluster, int coop_threshold, int 
 {
     if (!b)
         return fail(SR_EINVAL, "sr_batch_set_tuning: NULL batch");
-    if ((cluster != 1 && cluster != 2 && cluster != 4) || coop_threshold < 1 || ctas_per_sm < 1 || ctas_per_sm > 8)
-        return fail(SR_EINVAL, "sr_batch_set_tuning: cluster in {1,2,4}, threshold >= 1, 1 <= ctas_per_sm <= 8");
+    if ((cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4) || coop_threshold < 1 || ctas_per_sm < 1 ||
+        ctas_per_sm > 8)
+        return fail(SR_EINVAL, "sr_batch_set_tuning: cluster in {0,1,2,4} (0: grouped launches per pivot block), "
+                               "threshold >= 1, 1 <= ctas_per_sm <= 8");
     BatchPlan &p = b->plan;
     p.nc = cluster;
     p.coop_threshold = coop_threshold;
     p.ctas_per_sm = ctas_per_sm;
     if (p.exec) { cudaGraphExecDestroy(p.exec); p.exec = nullptr; }
     if (p.graph) { cudaGraphDestroy(p.graph); p.graph = nullptr; }
+    if (cluster == 0)
+        SR_TRY(build_grouped(p));            // device arrays now, never during a capture
     return build_items(p);
 }
 
@@ -599,6 +704,8 @@ sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream)
     if (!use_graph)
         return enqueue_batch(p, s);
     if (!p.exec) {
+        if (p.nc == 0)
+            SR_TRY(build_grouped(p));        // allocates: must precede the capture
         // capture counter reset + persistent kernel once, on a private stream
         cudaStream_t cs;
         SR_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -639,6 +746,9 @@ void sr_batch_destroy(sr_batch *b)
     if (p.d_graphs) cudaFree(p.d_graphs);
     if (p.d_items) cudaFree(p.d_items);
     if (p.d_counter) cudaFree(p.d_counter);
+    if (p.d_gactive) cudaFree(p.d_gactive);
+    if (p.d_gargs) cudaFree(p.d_gargs);
+    if (p.d_gstart) cudaFree(p.d_gstart);
     delete b;
 }
 
@@ -679,6 +789,7 @@ sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, do
     SR_CUDA_CHECK(cudaEventCreate(&e1));
     struct Cand { int nc, thr, cps; };
     std::vector<Cand> cands;
+    cands.push_back({0, 1 << 30, 1});                  // grouped launches per pivot block
     for (int cps : {1, 2})
         cands.push_back({1, 1 << 30, cps});
     for (int nc : {2, 4})

@@ -89,6 +89,13 @@ struct BatchItem {
     int g[4];
 };
 // One persistent launch without clusters: item i closes graph items[i].g[0] on one CTA.
+// The batched closure's grouped schedule (antidist.cu): many products in one launch, CTA b
+// taking tile b - start[i] of product args[i] (thin: 64x64 tiles, else 128x128); block kb
+// of graphs[active[0..n)] closed by one CTA each (phase 3 of kb-1 already applied).
+sr_status launch_antidist_mul_grouped(const MulArgs *args, const int *start, int n, int tiles, sr_dtype dt,
+                                      bool vec, bool thin, cudaStream_t s);
+sr_status launch_antidist_pivot_grouped(const BatchGraph *graphs, const int *active, int n, int kb, sr_dtype dt,
+                                        cudaStream_t s);
 sr_status launch_batched_closure_flat(sr_dtype dt, const BatchGraph *d_graphs, const BatchItem *d_items, int nitems,
                                       int *d_counter, int ctas_per_sm, cudaStream_t s);
 

@@ -51,9 +51,11 @@ SIZES = [1, 5, 31, 32, 33, 64, 65, 100, 127, 128, 129, 200, 257, 300, 450, 513, 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dt", [np.uint16, np.uint8])
-@pytest.mark.parametrize("tuning", [(1, 1 << 30, 1), (2, 128, 2), (4, 256, 1), (4, 64, 2), (2, 1, 1)])
+@pytest.mark.parametrize("tuning", [(1, 1 << 30, 1), (2, 128, 2), (4, 256, 1), (4, 64, 2), (2, 1, 1), (0, 1, 1)])
 @pytest.mark.parametrize("align", [False, True])
 def test_batched_matches_oracle(dt, tuning, align):
+    """Persistent kernel (clusters of 1, 2 or 4 CTAs, cooperative thresholds) and the
+    grouped schedule (cluster 0: launches per pivot block over all graphs)."""
     mats = make_batch(SIZES, dt, seed=len(SIZES) + tuning[0] * 10 + tuning[1] % 97)
     got = run_batch(mats, tuning=tuning, align=align)
     S = S_OF[dt]
@@ -74,6 +76,16 @@ def test_batched_graph_replay_autotune_and_padding():
         got = run_batch(make_batch([40, 300, 77, 640, 128, 9], np.uint16, seed=4), autotune=True, ctx=ctx)
     finally:
         sr.sr_destroy(ctx)
+
+
+@pytest.mark.gpu
+def test_batched_grouped_schedule_in_cuda_graph():
+    """The grouped schedule captured once into a CUDA graph and replayed on closed graphs
+    (idempotent), with a mix of single-block and multi-block graphs and unaligned rows."""
+    mats = make_batch([3, 128, 129, 600, 1000, 64, 257], np.uint16, seed=9)
+    got = run_batch(mats, tuning=(0, 1, 1), use_graph=True, launches=2, pad=3)
+    for M, G in zip(mats, got):
+        assert np.array_equal(G, oracle.warshall(M, 65535)), f"D={M.shape[0]}"
 
 
 @pytest.mark.gpu
