@@ -123,7 +123,7 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
     const int tiles_n = (p.N + BN - 1) / BN, tiles = tiles_n * ((p.R + BM - 1) / BM);
     const int nkt = (p.K + BK - 1) / BK;
 
-    // tiles in row-major order; a persistent grid (gridDim.x < tiles) walks them round-robin.
+    // tiles tile0, tile0 + stride, ... of the row-major tile grid (one per CTA when stride >= tiles)
     // skip_tile names a block of the 128x128 tile grid, which every tile shape here nests in.
     static_assert(128 % BM == 0 && 128 % BN == 0, "tiles nest in the 128x128 grid of skip_tile");
     const int tn128 = (p.N + 127) / 128;
@@ -706,28 +706,8 @@ __global__ void __launch_bounds__(256) antidist_pivot_grouped_kernel(const Batch
 // -------------------------------------------------------------------------
 // Host launchers
 // -------------------------------------------------------------------------
-// Sets the kernel's shared-memory attribute once per device and reports how many CTAs
-// of it fit on one SM.
 template <class KD, int BM, int BN, int BK, int TM, int TN>
-static sr_status mul_cfg_occupancy(bool vec, int &occ_out)
-{
-    using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
-    auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
-                    : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
-    static int occ[2][kMaxDevices] = {};
-    const int dev = current_device();
-    if (!occ[vec][dev]) {
-        SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-        int n = 0;
-        SR_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Cfg::THREADS, Cfg::SMEM));
-        occ[vec][dev] = n > 0 ? n : 1;
-    }
-    occ_out = occ[vec][dev];
-    return SR_OK;
-}
-
-template <class KD, int BM, int BN, int BK, int TM, int TN>
-static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int reserve_sms = 0)
+static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
     const int64_t tiles = (int64_t)((a.N + BN - 1) / BN) * ((a.R + BM - 1) / BM);
@@ -735,14 +715,15 @@ static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s, int 
         return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
     auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
                     : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
-    int occ = 1;
-    SR_TRY((mul_cfg_occupancy<KD, BM, BN, BK, TM, TN>(vec, occ)));
-    int64_t grid = tiles;
-    if (reserve_sms > 0) {   // persistent: leave reserve_sms SMs free for concurrent work
-        const int64_t slots = (int64_t)std::max(1, device_sm_count() - reserve_sms) * occ;
-        grid = std::min(tiles, slots);
+    static bool attr[2][kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[vec][dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        attr[vec][dev] = true;
     }
-    kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+    // one tile per CTA: the hardware block scheduler balances a sparse last wave better than
+    // a persistent grid or smaller tail tiles on a second stream (both measured slower)
+    kern<<<(unsigned)tiles, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
@@ -757,8 +738,6 @@ sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStrea
     if (tiles == 1)
         return dt == SR_U8 ? launch_mul_cfg<KindU8, 64, 64, 32, 4, 8>(a, vec, s)
                            : launch_mul_cfg<KindU16, 64, 64, 32, 4, 8>(a, vec, s);
-    // hardware block scheduling balances a sparse last wave of 128x128 tiles better than
-    // splitting it into smaller tiles on a second stream (measured on GB300)
     return dt == SR_U8 ? launch_mul_cfg<KindU8, 128, 128, 32, 8, 16>(a, vec, s)
                        : launch_mul_cfg<KindU16, 128, 128, 32, 8, 16>(a, vec, s);
 }

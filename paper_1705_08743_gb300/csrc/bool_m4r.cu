@@ -176,7 +176,7 @@ sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s)
 {
     if (a.R <= 0 || a.ncw <= 0)
         return SR_OK;
-    if (a.skipw || a.skipww || a.kr0 >= 0)
+    if (a.skipw || a.skipww)
         return fail(SR_EINVAL, "bool_mul (Four Russians): excluded ranges are not supported");
     return launch_m4r_cfg<kM4rWarps>(a, s);
 }

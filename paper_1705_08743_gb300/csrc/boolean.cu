@@ -185,7 +185,7 @@ bool_mul_kernel(BoolArgs p)
 #pragma unroll
         for (int u = 0; u < TNW; ++u) {
             const int w = w0 + (u / 4) * (4 * TC) + tc * 4 + (u % 4);
-            if (w < p.ncw && !(r >= p.kr0 && r < p.kr0 + p.krn && w >= p.kw0 && w < p.kw0 + p.kwn)) {
+            if (w < p.ncw) {
                 const int pw = bremap(w, p.skip0w, p.skipww);
                 const uint32_t m = word_mask(pw, p.N), v = acc[i][u] & m;
                 if (p.ksplit == 1) {
@@ -375,7 +375,7 @@ sr_status launch_bool_mul(const BoolArgs &in, bool vec, cudaStream_t s, int shap
     a.ksplit = 1;
     if (shape == 0) {
         // few output tiles (small products): narrower tiles, then split K across CTAs
-        const bool plain = a.skipww == 0 && a.skipw == 0 && a.kr0 < 0;
+        const bool plain = a.skipww == 0 && a.skipw == 0;
         if (a.ncw <= 16 && plain) shape = 2;
         const int bm = shape == 2 ? 32 : 128, bnw = shape == 2 ? 16 : 64;
         const int64_t tiles = (int64_t)((a.ncw + bnw - 1) / bnw) * ((a.R + bm - 1) / bm);

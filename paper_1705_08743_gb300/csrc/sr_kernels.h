@@ -33,8 +33,8 @@ struct MulArgs {
     int skip_tile = -1;        // a tile (row-major index, 128x128 tiles) left untouched, or -1
 };
 
-// tiles: 0 = 128x128 CTA tiles (throughput), 1 = 64x64 (latency: more CTAs for small grids),
-//        2 = 128x128 on a persistent grid that leaves one SM free for concurrent work
+// tiles: 0 = 128x128 CTA tiles (throughput; u32: 128x64), 1 = 64x64 (latency: more CTAs for
+//        thin panels and small grids)
 sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
 sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s);
 // u32 kernels (antidist32.cu), reached through launch_antidist_mul / launch_antidist_closure
@@ -55,8 +55,6 @@ struct BoolArgs {
     int accumulate;
     int skip0, skipw;          // excluded row range (rows of A and C)
     int skip0w, skipww;        // excluded word range (words of B and C)
-    int kr0 = -1, krn = 0;     // a block of C left unwritten: logical rows [kr0, kr0+krn) ...
-    int kw0 = 0, kwn = 0;      // ... and logical words [kw0, kw0+kwn) (kr0 = -1: none)
     int ksplit = 1;            // CTAs along K (set by launch_bool_mul; partial results ORed into C)
 };
 // shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
@@ -65,7 +63,7 @@ sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape
 size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N);
 bool bool_tc_available();
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s);
-// Four Russians (bool_m4r.cu): plain products only (no excluded ranges or keep-out block)
+// Four Russians (bool_m4r.cu): plain products only (no excluded ranges)
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
