@@ -22,8 +22,8 @@
 // row's byte), so table reads are free of bank conflicts.  A word of A (4 groups) is
 // loaded by the lane whose index is the row's and broadcast with shuffles.
 //
-// Only plain products (no excluded ranges) take this path; the result is bit-identical
-// to the masked-OR kernel: the Boolean product has one value.
+// Excluded row and word ranges (closure phase 3) are remapped as in the masked-OR kernel;
+// the result is bit-identical to it: the Boolean product has one value.
 
 #include <algorithm>
 
@@ -39,6 +39,8 @@ __device__ __forceinline__ uint32_t m4r_word_mask(int w, int nbits)
     if (lo >= nbits) return 0u;
     return (1u << (nbits - lo)) - 1u;
 }
+
+__device__ __forceinline__ int m4r_remap(int x, int skip0, int skipw) { return x < skip0 ? x : x + skipw; }
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 constexpr int kM4rWarps = 8;     // warps per CTA (rows per CTA: 32 per warp)
@@ -98,8 +100,9 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) bool_m4r_kerne
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row0 = blockIdx.y * (32 * WARPS) + warp * 32;
-    const int w = blockIdx.x * 32 + lane;
+    const int w = blockIdx.x * 32 + lane;                         // logical word of B and C
     const bool wok = w < p.ncw;
+    const int pw = m4r_remap(w, p.skip0w, p.skipww);              // its physical word
     const int K = p.K, G = (K + 7) / 8, NKW = (K + 31) / 32;
     const uint32_t *__restrict__ Bm = p.B;
     const int64_t ldb = p.ldb;
@@ -108,21 +111,22 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) bool_m4r_kerne
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         const int r = row0 + j;
-        acc[j] = (p.accumulate && wok && r < p.R) ? p.C[(int64_t)r * p.ldc + w] : 0u;
+        acc[j] = (p.accumulate && wok && r < p.R) ? p.C[(int64_t)m4r_remap(r, p.skip0, p.skipw) * p.ldc + pw] : 0u;
     }
 
     uint32_t nb[8];                              // rows of B of the next table to build
-    m4r_loadB(nb, Bm, ldb, K, 0, w, wok);
+    m4r_loadB(nb, Bm, ldb, K, 0, pw, wok);
     m4r_build<EPW, LB>(nb, T, warp, lane);
-    if (G > 1) m4r_loadB(nb, Bm, ldb, K, 1, w, wok);
+    if (G > 1) m4r_loadB(nb, Bm, ldb, K, 1, pw, wok);
     const int rl = row0 + lane;                  // the row whose A words this lane loads
-    uint32_t anext = (rl < p.R && NKW > 0) ? __ldg(p.A + (int64_t)rl * p.lda) : 0u;
+    const int64_t prl = m4r_remap(rl, p.skip0, p.skipw);
+    uint32_t anext = (rl < p.R && NKW > 0) ? __ldg(p.A + prl * p.lda) : 0u;
     __syncthreads();
 
     for (int kw = 0; kw < NKW; ++kw) {
         const uint32_t amine = anext;
         if (kw + 1 < NKW)
-            anext = rl < p.R ? __ldg(p.A + (int64_t)rl * p.lda + kw + 1) : 0u;
+            anext = rl < p.R ? __ldg(p.A + prl * p.lda + kw + 1) : 0u;
         uint32_t aw[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j)
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) bool_m4r_kerne
                 break;                           // uniform across the CTA
             if (g + 1 < G) {
                 m4r_build<EPW, LB>(nb, T + ((g + 1) & 1) * TW, warp, lane);
-                if (g + 2 < G) m4r_loadB(nb, Bm, ldb, K, g + 2, w, wok);
+                if (g + 2 < G) m4r_loadB(nb, Bm, ldb, K, g + 2, pw, wok);
             }
             const uint32_t *Tb = T + (g & 1) * TW + lane;
 #pragma unroll
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) bool_m4r_kerne
     for (int j = 0; j < 32; ++j) {
         const int r = row0 + j;
         if (wok && r < p.R)
-            p.C[(int64_t)r * p.ldc + w] = acc[j] & m4r_word_mask(w, p.N);
+            p.C[(int64_t)m4r_remap(r, p.skip0, p.skipw) * p.ldc + pw] = acc[j] & m4r_word_mask(pw, p.N);
     }
 }
 
@@ -176,8 +180,6 @@ sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s)
 {
     if (a.R <= 0 || a.ncw <= 0)
         return SR_OK;
-    if (a.skipw || a.skipww)
-        return fail(SR_EINVAL, "bool_mul (Four Russians): excluded ranges are not supported");
     return launch_m4r_cfg<kM4rWarps>(a, s);
 }
 

@@ -469,6 +469,8 @@ static BoolArgs bool_args(const uint32_t *A, const uint32_t *B, uint32_t *C, int
 // pivot kb), apply pivot kb to block row kb+1 and block column kb+1, and then compute
 // the row and column panels of kb+1 (monotone OR updates make the in-place read/write
 // overlap of a panel product harmless).
+constexpr int kM4rPhase3MinRows = 2048;
+
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
 {
     constexpr int PB = 128, PW = PB / 32;
@@ -537,10 +539,14 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
             SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
             SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
         }
-        // phase 3 of kb: rows and words outside blocks kb, kb+1
+        // phase 3 of kb: rows and words outside blocks kb, kb+1 (Four Russians tables on
+        // large matrices)
         BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D - ex, bw, D, rw - exw);
         p3.skip0 = k0; p3.skipw = ex; p3.skip0w = kw; p3.skipww = exw;
-        SR_TRY(launch_bool_mul(p3, vec, s));
+        if (D - ex >= kM4rPhase3MinRows)
+            SR_TRY(launch_bool_mul_m4r(p3, s));
+        else
+            SR_TRY(launch_bool_mul(p3, vec, s));
         if (!next)
             break;
         SR_CUDA_CHECK(cudaEventRecord(main_done[kb], s));

@@ -63,7 +63,7 @@ sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape
 size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N);
 bool bool_tc_available();
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s);
-// Four Russians (bool_m4r.cu): plain products only (no excluded ranges)
+// Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,

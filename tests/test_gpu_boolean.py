@@ -144,6 +144,17 @@ def test_bool_closure(w, D, sq_ctx):
             assert np.array_equal(unpacked(got, w, D), ref), (p, method)
 
 
+@pytest.mark.parametrize("w,D", [(64, 2500), (32, 2333)])
+def test_bool_closure_four_russians_phase3(w, D):
+    """From D = 2304 on, phase 3 runs on the Four Russians tables with the rows and words
+    of the two pivot blocks left out by remapping; Warshall form, every word compared."""
+    import paper_1705_08743_gb300 as sr
+    dense = synth.bool_dag_union(D, seed=D)
+    got = gpu_bool_closure(dense, w, sr.SR_CLOSURE_WARSHALL)
+    want = oracle.bool_warshall_w64(oracle.pack_bits(dense))
+    assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want)
+
+
 def test_bool_closure_pad_and_unaligned(sq_ctx):
     import paper_1705_08743_gb300 as sr
     rng = np.random.default_rng(9)
