@@ -297,8 +297,21 @@ class Cfg4:
 
     dtype = "u16"
     only = ""
-    roofline_kernel = "batched_closure_kernel<KindU16,64,NC>"
-    roofline_sources = ["paper_1705_08743_gb300/csrc/batched.cu", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
+    tuning = (2, 384, 2)
+
+    # the dominant kernels follow the schedule the autotuner picked (cluster 0: grouped)
+    @property
+    def roofline_kernel(self):
+        if self.tuning[0] == 0:
+            return "grouped schedule: antidist_mul_grouped_kernel<KindU16> + antidist_pivot_grouped_kernel<KindU16,128>"
+        return "batched_closure_kernel<KindU16,64,NC>"
+
+    @property
+    def roofline_sources(self):
+        src = ["paper_1705_08743_gb300/csrc/batched.cu", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
+        if self.tuning[0] == 0:
+            src.append("paper_1705_08743_gb300/csrc/antidist.cu")
+        return src
 
     fixed_tuning = None
 
