@@ -265,7 +265,9 @@ typedef struct {
 /* Start the loop on ctx's device: allocates the arena (one cudaMalloc), per-slot
  * streams and staging buffers, and a scheduler thread.  Requests are admitted in
  * submission order as stream slots and arena memory free up (continuous
- * batching); waiting small closures of one dtype join one batched launch. */
+ * batching); waiting small closures of one dtype join one batched launch.  A request
+ * estimated to take a millisecond or more of device time waits while another such
+ * request is in flight (two would slow each other down); shorter ones run beside it. */
 sr_status sr_serve_start(sr_ctx *ctx, const sr_serve_config *cfg);
 /* Stop the loop (waits for admitted work), free its memory; also done by sr_destroy. */
 sr_status sr_serve_stop(sr_ctx *ctx);

@@ -132,6 +132,7 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     bool busy = false;
+    bool long_job = false;                 // holds the one long request allowed in flight
     // batched-group staging
     BatchGraph *d_graphs = nullptr;
     BatchItem *d_items = nullptr;
@@ -164,7 +165,21 @@ struct ServeState {
     // stats
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_reqs = 0;
     int inflight = 0;
+    int long_inflight = 0;
 };
+
+// Requests expected to keep the GPU busy for a millisecond or more run one at a time:
+// two of them sharing the device would each take about twice as long, which is what
+// the tail latency is made of; short requests still fill the other slots around them.
+// The estimate is the operation count over the kernels' measured rates on GB300.
+static bool is_long(const sr_request &r)
+{
+    const sr_dtype t = (sr_dtype)r.dtype;
+    const bool closure = r.op == SR_OP_ANTIDIST_CLOSURE || r.op == SR_OP_BOOL_CLOSURE;
+    const double ops = closure ? (double)r.R * r.R * r.R : (double)r.R * r.K * r.N;
+    const double rate = t == SR_U8 ? 3.0e13 : t == SR_U16 ? 1.5e13 : t == SR_U32 ? 8.0e12 : 4.0e14;   // ops/s
+    return ops / rate >= 1.0e-3;
+}
 
 static int es_of(sr_dtype t) { return t == SR_U8 ? 1 : t == SR_U16 ? 2 : (t == SR_BOOL_W32 || t == SR_U32) ? 4 : 8; }
 static int64_t units_of(sr_dtype t, int64_t n)
@@ -212,6 +227,10 @@ static void CUDART_CB on_complete(void *arg)
             ++st->completed;
         }
         st->slots[c->slot].busy = false;
+        if (st->slots[c->slot].long_job) {
+            st->slots[c->slot].long_job = false;
+            --st->long_inflight;
+        }
         --st->inflight;
     }
     st->cv_sched.notify_one();
@@ -350,8 +369,9 @@ static std::vector<size_t> buffer_sizes(const sr_request &r)
 }
 
 // Pick the next job that fits now (lock held): a free slot, then the head request,
-// or with backfill a later one whose buffers fit; small closures of the head's dtype
-// waiting behind it join its group.  Allocates the buffers; false if nothing fits.
+// or with backfill a later one whose buffers fit (a long request also waits while
+// another long one is in flight); small closures of the head's dtype waiting behind it
+// join its group.  Allocates the buffers; false if nothing fits.
 static bool next_job(ServeState &st, Job &job)
 {
     int slot = -1;
@@ -364,7 +384,10 @@ static bool next_job(ServeState &st, Job &job)
     int pick = -1;
     for (int i = 0; i < (int)st.pending.size(); ++i) {
         const Req &q = *st.reqs[st.pending[i]];
-        if (request_bytes(q.r) <= st.arena.largest_free()) { pick = i; break; }
+        if (request_bytes(q.r) <= st.arena.largest_free() && !(st.long_inflight > 0 && is_long(q.r))) {
+            pick = i;
+            break;
+        }
         if (!may_backfill) break;
     }
     if (pick < 0) return false;
@@ -413,6 +436,10 @@ static bool next_job(ServeState &st, Job &job)
         if (r.rB) { const Resident &x = st.residents[r.rB]; job.inB = st.base + x.off; job.ldB = x.ld; }
     }
     st.slots[slot].busy = true;
+    if (!job.group && is_long(job.reqs[0]->r)) {
+        st.slots[slot].long_job = true;
+        ++st.long_inflight;
+    }
     ++st.inflight;
     return true;
 }
