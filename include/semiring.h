@@ -106,10 +106,16 @@ typedef enum {
     SR_OPT_BOOL_TENSOR = 1,  /* Boolean products on the tensor cores (count, then test > 0):
                                 0 never, 1 when K >= 1024 (default), 2 whenever possible.
                                 Used only with enough ctx workspace (sr_workspace_query). */
-    SR_OPT_BOOL_FOUR_RUSSIANS = 2  /* Boolean products off the tensor cores by the method of
+    SR_OPT_BOOL_FOUR_RUSSIANS = 2, /* Boolean products off the tensor cores by the method of
                                 Four Russians (8-bit groups of K, 256-entry OR tables of
                                 rows of B; Section 4 names the method for the product):
                                 0 never, 1 for large products (default), 2 always. */
+    SR_OPT_SPIN_LIMIT = 3    /* tries per bounded device-side wait (the tensor-core pipeline's
+                                mbarrier waits); a wait that gives up sets the context's status
+                                word, which sr_stream_status reports as SR_ETIMEOUT, and the CTA
+                                drains the copies and MMAs it started and returns.  0 makes
+                                every wait give up at once (fault injection for tests); the
+                                default is sr_config.spin_limit. */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 

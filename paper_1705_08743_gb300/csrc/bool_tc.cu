@@ -34,7 +34,7 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK;
 constexpr size_t SMEM = 1024 + (size_t)STAGES * (A_BYTES + B_BYTES) + 128;
 constexpr int TMEM_COLS = 256;
-constexpr uint32_t SPIN_LIMIT = 1u << 22;     // tries per wait before giving up
+constexpr uint32_t DRAIN_LIMIT = 1u << 24;    // tries per wait for work already started, on the failure path
 constexpr int GROUP_M = 16;                  // tile rows per rasterisation group
 }  // namespace tc
 
@@ -47,6 +47,7 @@ struct BoolTcArgs {
     int tiles_m, tiles_n; // output tiles (BM rows, BN columns)
     int accumulate;
     int *status;          // nonzero after a bounded wait gave up (may be null)
+    uint32_t wait_limit;  // tries per wait before giving up (the context's spin limit)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -59,10 +60,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
-// true once the phase with the given parity has completed; false after SPIN_LIMIT tries
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// true once the phase with the given parity has completed; false after `limit` tries
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t it = 0; it < tc::SPIN_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -162,7 +163,7 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     if (warp == 0 && lane == 0) {
         for (int kb = 0; kb < p.nkb; ++kb) {
             const int s = kb % tc::STAGES;
-            if (kb >= tc::STAGES && !mbar_wait(empty0 + 8 * s, ((kb / tc::STAGES) - 1) & 1)) {
+            if (kb >= tc::STAGES && !mbar_wait(empty0 + 8 * s, ((kb / tc::STAGES) - 1) & 1, p.wait_limit)) {
                 atomicExch(&failed, 1);
                 break;
             }
@@ -175,7 +176,7 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     } else if (warp == 1 && lane == 0) {
         for (int kb = 0; kb < p.nkb; ++kb) {
             const int s = kb % tc::STAGES;
-            if (!mbar_wait(full0 + 8 * s, (kb / tc::STAGES) & 1)) {
+            if (!mbar_wait(full0 + 8 * s, (kb / tc::STAGES) & 1, p.wait_limit)) {
                 atomicExch(&failed, 1);
                 break;
             }
@@ -191,7 +192,7 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     __syncwarp();
 
     // epilogue: 32 accumulator lanes per warp, 32 columns per tensor-memory load
-    const bool ok = mbar_wait(done, 0);
+    const bool ok = mbar_wait(done, 0, p.wait_limit);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!ok) atomicExch(&failed, 1);
     __syncthreads();
@@ -214,12 +215,16 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     }
     if (!good) {
         if (tid == 0 && p.status) atomicExch(p.status, 1);
-        // drain: every TMA copy this CTA started must land before its shared memory is released
-        if (warp == 0 && lane == 0)
+        // drain: every TMA copy this CTA started must land before its shared memory is
+        // released, and every MMA it issued must finish before its tensor memory is freed
+        // (done arrives once they have); these waits have their own, longer, bound
+        if (warp == 0 && lane == 0) {
             for (int s = 0; s < tc::STAGES && s < nload; ++s) {
                 const int loads = (nload - 1 - s) / tc::STAGES + 1;      // loads issued to stage s
-                mbar_wait(full0 + 8 * s, (loads - 1) & 1);
+                mbar_wait(full0 + 8 * s, (loads - 1) & 1, tc::DRAIN_LIMIT);
             }
+            mbar_wait(done, 0, tc::DRAIN_LIMIT);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -328,7 +333,8 @@ bool bool_tc_available()
     return major == 10 && encode_fn() != nullptr;
 }
 
-sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s)
+sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
+                             cudaStream_t s)
 {
     const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
     if (bool_tc_workspace(a.R, a.K, a.N) > ws_bytes)
@@ -366,6 +372,7 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     p.nkb = Kp / tc::BK;
     p.accumulate = a.accumulate;
     p.status = status;
+    p.wait_limit = (uint32_t)std::max(0, spin_limit);
     p.tiles_n = (a.ncw + tc::BN / 32 - 1) / (tc::BN / 32);
     p.tiles_m = (a.R + tc::BM - 1) / tc::BM;
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;

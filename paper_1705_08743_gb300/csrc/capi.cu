@@ -193,6 +193,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->bool_m4r_mode = value;
         return SR_OK;
     }
+    if (option == SR_OPT_SPIN_LIMIT && value >= 0) {
+        c->spin_limit = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -334,7 +338,7 @@ static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_
     a.skip0 = 0x7fffffff; a.skipw = 0;
     a.skip0w = 0x7fffffff; a.skipww = 0;
     if (use_tc(ctx, R, K, N, ws_bytes))
-        return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, s);
+        return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, ctx->spin_limit, s);
     if (use_m4r(ctx, R, K, a.ncw))
         return launch_bool_mul_m4r(a, s);
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
@@ -416,7 +420,7 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
         a.skip0 = 0x7fffffff; a.skipw = 0;
         a.skip0w = 0x7fffffff; a.skipww = 0;
         if (tcpath)
-            return launch_bool_mul_tc(a, tcws, tcbytes, c->d_status, s);
+            return launch_bool_mul_tc(a, tcws, tcbytes, c->d_status, c->spin_limit, s);
         const bool v = aligned16(X) && aligned16(Y) && ((ldx & 3) == 0) && ((ldy & 3) == 0);
         return launch_bool_mul(a, v, s);
     };

@@ -62,7 +62,10 @@ sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape
 // Tensor-core Boolean product (bool_tc.cu): workspace bytes, availability, launch.
 size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N);
 bool bool_tc_available();
-sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, cudaStream_t s);
+// spin_limit: tries per bounded wait (0: every wait gives up at once); a wait that gives up
+// sets *status and the CTA drains what it started and returns
+sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
+                             cudaStream_t s);
 // Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);

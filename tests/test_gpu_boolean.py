@@ -289,3 +289,32 @@ def test_bool_mul_four_russians_default_large():
     want = oracle.bool_mul_w64(A64, B64, N)
     assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want)
     assert want.any()
+
+
+def test_tensor_path_bounded_wait_gives_up_and_recovers():
+    """Fault injection without a GPU fault: with a spin limit of 0 every mbarrier wait of
+    the tensor-core pipeline gives up at once; each CTA drains the copies and MMAs it
+    started, frees its tensor memory and returns, and the context's status word reports
+    SR_ETIMEOUT.  The same context then computes the right product with the limit back."""
+    import paper_1705_08743_gb300 as sr
+    R = K = N = 1024
+    rng = np.random.default_rng(1024)
+    A, B = rand_bool(rng, R, K, 0.01), rand_bool(rng, K, N, 0.01)
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_MUL, sr.SR_BOOL_W64, R) + 4096)
+    try:
+        sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 2)
+        Ad, Bd = to_dev(packed(A, 64)), to_dev(packed(B, 64))
+        Cd = to_dev(np.zeros_like(packed(np.zeros((R, N), np.uint8), 64)))
+        sr.sr_set_option(ctx, sr.SR_OPT_SPIN_LIMIT, 0)
+        sr.bool_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, sr.SR_BOOL_W64, 0)
+        with pytest.raises(sr.SemiringError) as e:
+            sr.sr_stream_status(ctx)
+        assert e.value.status == sr.SR_ETIMEOUT
+        sr.sr_stream_status(ctx)                          # reading the status cleared it
+        sr.sr_set_option(ctx, sr.SR_OPT_SPIN_LIMIT, 1 << 22)
+        sr.bool_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, sr.SR_BOOL_W64, 0)
+        sr.sr_stream_status(ctx)
+        got = unpacked(to_host(Cd, np.uint64), 64, N)
+        assert np.array_equal(got, oracle.mul(A, B, 1))
+    finally:
+        sr.sr_destroy(ctx)
