@@ -52,7 +52,8 @@ typedef enum {
     SR_ETIMEOUT = 4,   /* a bounded device-side or host-side wait gave up */
     SR_EAGAIN = 5,     /* serving: no free slot or memory now; retry later */
     SR_EBUSY = 6,      /* serving: ticket not finished yet */
-    SR_ENOTFOUND = 7   /* serving: unknown or already released ticket */
+    SR_ENOTFOUND = 7,  /* serving: unknown or already released ticket */
+    SR_ECANCELED = 8   /* serving: the request was cancelled before it ran (sr_cancel) */
 } sr_status;
 
 typedef enum {
@@ -263,7 +264,7 @@ typedef struct {
 } sr_result_info;
 
 typedef struct {
-    uint64_t submitted, completed, failed, batches, batched_requests;
+    uint64_t submitted, completed, failed, batches, batched_requests, cancelled;
     size_t arena_bytes, arena_in_use, arena_peak_bytes;
     int pending, inflight, residents;
 } sr_serve_stats_t;
@@ -284,6 +285,11 @@ sr_status sr_poll(sr_ctx *ctx, uint64_t ticket, int *done);
 /* Block until done or timeout_ms elapsed (SR_ETIMEOUT); returns the request's status. */
 sr_status sr_wait(sr_ctx *ctx, uint64_t ticket, int timeout_ms);
 sr_status sr_result(sr_ctx *ctx, uint64_t ticket, sr_result_info *info);
+/* Withdraw a waiting request: it leaves the queue without running, and sr_wait /
+ * sr_result then report SR_ECANCELED for it (its output buffer is not written).
+ * SR_EBUSY: already admitted (running requests finish); SR_OK without effect on a
+ * finished ticket; SR_ENOTFOUND: unknown ticket.  The ticket still needs sr_release. */
+sr_status sr_cancel(sr_ctx *ctx, uint64_t ticket);
 /* Forget a finished ticket (a kept result stays resident until sr_resident_free). */
 sr_status sr_release(sr_ctx *ctx, uint64_t ticket);
 /* Resident matrices (in the arena): upload (blocking), download (synchronises the

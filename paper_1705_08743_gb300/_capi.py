@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 # status codes / enums (include/semiring.h)
-SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ETIMEOUT, SR_EAGAIN, SR_EBUSY, SR_ENOTFOUND = range(8)
+SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ETIMEOUT, SR_EAGAIN, SR_EBUSY, SR_ENOTFOUND, SR_ECANCELED = range(9)
 SR_BOOL_W32, SR_BOOL_W64, SR_U8, SR_U16, SR_U32 = range(5)
 SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
 SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
@@ -36,7 +36,7 @@ SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 
 STATUS_NAMES = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ETIMEOUT",
-                5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND"}
+                5: "SR_EAGAIN", 6: "SR_EBUSY", 7: "SR_ENOTFOUND", 8: "SR_ECANCELED"}
 
 
 class SemiringError(RuntimeError):
@@ -77,7 +77,7 @@ class sr_result_info(ctypes.Structure):
 
 class sr_serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
-                ("batches", ctypes.c_uint64), ("batched_requests", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("batched_requests", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
                 ("arena_bytes", ctypes.c_size_t), ("arena_in_use", ctypes.c_size_t),
                 ("arena_peak_bytes", ctypes.c_size_t), ("pending", ctypes.c_int), ("inflight", ctypes.c_int),
                 ("residents", ctypes.c_int)]
@@ -121,6 +121,7 @@ _SIGS = {
     "sr_wait": (_st, [_vp, ctypes.c_uint64, _int]),
     "sr_result": (_st, [_vp, ctypes.c_uint64, ctypes.POINTER(sr_result_info)]),
     "sr_release": (_st, [_vp, ctypes.c_uint64]),
+    "sr_cancel": (_st, [_vp, ctypes.c_uint64]),
     "sr_resident_put": (_st, [_vp, _vp, _i64, _i64, _int, ctypes.POINTER(ctypes.c_uint64)]),
     "sr_resident_get": (_st, [_vp, ctypes.c_uint64, _vp]),
     "sr_resident_free": (_st, [_vp, ctypes.c_uint64]),
@@ -351,6 +352,10 @@ def sr_result(ctx, ticket):
 
 def sr_release(ctx, ticket):
     _check(lib.sr_release(ctx, ticket), "sr_release")
+
+
+def sr_cancel(ctx, ticket):
+    _check(lib.sr_cancel(ctx, ticket), "sr_cancel")
 
 
 def sr_resident_put(ctx, host, rows, cols, dtype):

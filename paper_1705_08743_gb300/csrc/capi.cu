@@ -10,6 +10,7 @@
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 #include "sr_ctx.h"
 
 namespace sr {
@@ -220,6 +221,7 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
 
 sr_status sr_stream_status(sr_ctx *c, void *stream)
 {
+    SR_TRACE("sr_stream_status");
     if (!c)
         return fail(SR_EINVAL, "sr_stream_status: ctx is NULL");
     SR_CUDA_CHECK(cudaStreamSynchronize(S(stream)));
@@ -235,6 +237,7 @@ sr_status sr_stream_status(sr_ctx *c, void *stream)
 sr_status antidist_encode(sr_ctx *, const void *W, int64_t ldw, void *T, int64_t ldt, int64_t R, int64_t C,
                           sr_dtype dtype, void *stream)
 {
+    SR_TRACE("antidist_encode");
     const char *fn = "antidist_encode";
     if (!is_anti(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
@@ -248,6 +251,7 @@ sr_status antidist_encode(sr_ctx *, const void *W, int64_t ldw, void *T, int64_t
 sr_status bool_pack(sr_ctx *, const uint8_t *dense, int64_t ldd, void *M, int64_t ldm, int64_t R, int64_t C,
                     sr_dtype dtype, void *stream)
 {
+    SR_TRACE("bool_pack");
     const char *fn = "bool_pack";
     if (!is_bool(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
@@ -263,6 +267,7 @@ sr_status bool_pack(sr_ctx *, const uint8_t *dense, int64_t ldd, void *M, int64_
 sr_status bool_unpack(sr_ctx *, const void *M, int64_t ldm, uint8_t *dense, int64_t ldd, int64_t R, int64_t C,
                       sr_dtype dtype, void *stream)
 {
+    SR_TRACE("bool_unpack");
     const char *fn = "bool_unpack";
     if (!is_bool(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
@@ -278,6 +283,7 @@ sr_status bool_unpack(sr_ctx *, const void *M, int64_t ldm, uint8_t *dense, int6
 sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                        int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
 {
+    SR_TRACE("antidist_mul");
     const char *fn = "antidist_mul";
     if (!is_anti(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
@@ -348,6 +354,7 @@ static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_
 sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                    int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
 {
+    SR_TRACE("bool_mul");
     const char *fn = "bool_mul";
     if (!is_bool(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
@@ -368,6 +375,7 @@ sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64
 // ------------------------------------------------------------------ closures
 sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
+    SR_TRACE("antidist_closure");
     const char *fn = "antidist_closure";
     if (!is_anti(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
@@ -379,6 +387,7 @@ sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype d
 
 sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, int method, void *stream)
 {
+    SR_TRACE("bool_closure");
     const char *fn = "bool_closure";
     if (!is_bool(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
@@ -436,6 +445,7 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
 sr_status dist_mul(sr_ctx *c, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                    int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
 {
+    SR_TRACE("dist_mul");
     const char *fn = "dist_mul";
     if (!is_anti(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
@@ -475,6 +485,7 @@ sr_status dist_mul(sr_ctx *c, const void *A, int64_t lda, const void *B, int64_t
 
 sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
+    SR_TRACE("dist_closure");
     const char *fn = "dist_closure";
     if (!is_anti(dtype))
         return fail(SR_EINVAL, "%s: dtype must be SR_U8, SR_U16 or SR_U32", fn);
@@ -491,6 +502,7 @@ sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype
 sr_status sr_entrywise(sr_ctx *, int op, const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
                        int64_t ldc, int64_t R, int64_t N, sr_dtype dtype, void *stream)
 {
+    SR_TRACE("sr_entrywise");
     const char *fn = "sr_entrywise";
     if (op < SR_EW_AND || op > SR_EW_NOT)
         return fail(SR_EINVAL, "%s: unknown op %d", fn, op);
@@ -507,6 +519,7 @@ sr_status sr_entrywise(sr_ctx *, int op, const void *A, int64_t lda, const void 
 
 sr_status sr_reflexive(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
+    SR_TRACE("sr_reflexive");
     const char *fn = "sr_reflexive";
     if (!is_anti(dtype) && !is_bool(dtype))
         return fail(SR_EINVAL, "%s: unknown dtype", fn);

@@ -32,6 +32,7 @@
 #include "sr_common.cuh"
 #include "sr_ctx.h"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace sr {
 
@@ -163,7 +164,7 @@ struct ServeState {
     bool stop = false;
     std::thread th;
     // stats
-    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_reqs = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_reqs = 0, cancelled = 0;
     int inflight = 0;
     int long_inflight = 0;
 };
@@ -486,7 +487,11 @@ static void scheduler(ServeState *st)
         }
         cudaStream_t s = st->slots[job.slot].stream;
         lk.unlock();
-        const sr_status est = job.group ? enqueue_group(*st, job, s) : enqueue_request(*st, job, s);
+        sr_status est;
+        {
+            SR_TRACE(job.group ? "serve: grouped closures" : "serve: request");
+            est = job.group ? enqueue_group(*st, job, s) : enqueue_request(*st, job, s);
+        }
         const std::string msg = est == SR_OK ? std::string() : std::string(sr_last_error());
         lk.lock();
         finish_job(*st, job, est, msg.c_str());
@@ -539,6 +544,7 @@ extern "C" {
 
 sr_status sr_serve_start(sr_ctx *c, const sr_serve_config *cfg)
 {
+    SR_TRACE("sr_serve_start");
     if (!c)
         return fail(SR_EINVAL, "sr_serve_start: ctx is NULL");
     if (c->serve)
@@ -587,6 +593,7 @@ sr_status sr_serve_start(sr_ctx *c, const sr_serve_config *cfg)
 
 sr_status sr_serve_stop(sr_ctx *c)
 {
+    SR_TRACE("sr_serve_stop");
     if (!c)
         return fail(SR_EINVAL, "sr_serve_stop: ctx is NULL");
     stop_serving(c);
@@ -595,6 +602,7 @@ sr_status sr_serve_stop(sr_ctx *c)
 
 sr_status sr_submit(sr_ctx *c, const sr_request *r, uint64_t *ticket)
 {
+    SR_TRACE("sr_submit");
     if (!c || !r || !ticket)
         return fail(SR_EINVAL, "sr_submit: NULL argument");
     ServeState *st = c->serve;
@@ -649,6 +657,7 @@ sr_status sr_poll(sr_ctx *c, uint64_t ticket, int *done)
 
 sr_status sr_wait(sr_ctx *c, uint64_t ticket, int timeout_ms)
 {
+    SR_TRACE("sr_wait");
     if (!c || !c->serve)
         return fail(SR_EINVAL, "sr_wait: not serving");
     ServeState *st = c->serve;
@@ -685,6 +694,35 @@ sr_status sr_result(sr_ctx *c, uint64_t ticket, sr_result_info *info)
     return SR_OK;
 }
 
+sr_status sr_cancel(sr_ctx *c, uint64_t ticket)
+{
+    SR_TRACE("sr_cancel");
+    if (!c || !c->serve)
+        return fail(SR_EINVAL, "sr_cancel: not serving");
+    ServeState *st = c->serve;
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        auto it = st->reqs.find(ticket);
+        if (it == st->reqs.end())
+            return fail(SR_ENOTFOUND, "sr_cancel: unknown ticket %llu", (unsigned long long)ticket);
+        Req &q = *it->second;
+        if (q.done)
+            return SR_OK;                                   // finished (or cancelled) already
+        auto pos = std::find(st->pending.begin(), st->pending.end(), ticket);
+        if (pos == st->pending.end())
+            return fail(SR_EBUSY, "sr_cancel: ticket %llu is already running", (unsigned long long)ticket);
+        st->pending.erase(pos);                             // never admitted: it holds no memory or slot
+        q.status = SR_ECANCELED;
+        q.err = "cancelled before admission";
+        q.done = true;
+        q.t_admit = q.t_done = now_ms();
+        ++st->cancelled;
+    }
+    st->cv_done.notify_all();
+    st->cv_sched.notify_one();
+    return SR_OK;
+}
+
 sr_status sr_release(sr_ctx *c, uint64_t ticket)
 {
     if (!c || !c->serve)
@@ -702,6 +740,7 @@ sr_status sr_release(sr_ctx *c, uint64_t ticket)
 
 sr_status sr_resident_put(sr_ctx *c, const void *host, int64_t rows, int64_t cols, sr_dtype dtype, uint64_t *handle)
 {
+    SR_TRACE("sr_resident_put");
     if (!c || !c->serve || !host || !handle || rows <= 0 || cols <= 0)
         return fail(SR_EINVAL, "sr_resident_put: not serving or bad argument");
     ServeState *st = c->serve;
@@ -729,6 +768,7 @@ sr_status sr_resident_put(sr_ctx *c, const void *host, int64_t rows, int64_t col
 
 sr_status sr_resident_get(sr_ctx *c, uint64_t handle, void *host)
 {
+    SR_TRACE("sr_resident_get");
     if (!c || !c->serve || !host)
         return fail(SR_EINVAL, "sr_resident_get: not serving or NULL argument");
     ServeState *st = c->serve;
@@ -774,6 +814,7 @@ sr_status sr_serve_stats(sr_ctx *c, sr_serve_stats_t *out)
     out->failed = st->failed;
     out->batches = st->batches;
     out->batched_requests = st->batched_reqs;
+    out->cancelled = st->cancelled;
     out->arena_bytes = st->arena.size();
     out->arena_in_use = st->arena.used();
     out->arena_peak_bytes = st->arena.peak();

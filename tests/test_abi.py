@@ -52,3 +52,4 @@ def test_errors_without_device(lib):
     assert st == lib.SR_EINVAL and "NULL" in lib.last_error()
     st = lib.lib.bool_mul(None, 16, 1, 16, 1, 16, 1, 4, 4, 4, lib.SR_BOOL_W32, 0, None)
     assert st == lib.SR_EINVAL and "overlap" in lib.last_error()
+    assert lib.lib.sr_cancel(None, 1) == lib.SR_EINVAL and "not serving" in lib.last_error()

@@ -217,3 +217,49 @@ def test_wait_timeout_and_bad_requests():
         assert e.value.status == sr.SR_ENOTFOUND
     finally:
         sr.sr_destroy(ctx)
+
+
+def test_cancel_waiting_request():
+    """A request withdrawn while it waits never runs: its output stays untouched and
+    sr_wait reports SR_ECANCELED; the requests around it still match the oracle."""
+    sr = _sr()
+    rng = np.random.default_rng(5)
+    ctx = sr.sr_create()
+    try:
+        sr.sr_serve_start(ctx, arena_bytes=512 << 20, slots=1)
+        D = 1200                                     # the closure holds the one slot while the rest queue
+        A0 = pinned(rand_anti(rng, D, D, 65535, p=4.0 / D))
+        out0 = pinned(np.zeros((D, D), np.uint16))
+        prods = []
+        for i in range(4):                           # products queue behind it (products never group)
+            A, B = rand_anti(rng, 200, 150, 255, p=0.5), rand_anti(rng, 150, 230, 255, p=0.5)
+            prods.append([None, pinned(np.full((200, 230), 7, np.uint8)), oracle.mul(A, B, 255).astype(np.uint8),
+                          (pinned(A), pinned(B))])
+        t0 = sr.sr_submit(ctx, sr.make_request(sr.SR_OP_ANTIDIST_CLOSURE, sr.SR_U16, D, A=A0, out=out0))
+        for p in prods:
+            p[0] = sr.sr_submit(ctx, sr.make_request(sr.SR_OP_ANTIDIST_MUL, sr.SR_U8, 200, 150, 230, A=p[3][0],
+                                                     B=p[3][1], out=p[1]))
+        victim = prods[-1][0]                        # last in line: waits until the four before it finish
+        sr.sr_cancel(ctx, victim)
+        sr.sr_cancel(ctx, victim)                    # a second cancel changes nothing
+        with pytest.raises(sr.SemiringError) as e:
+            sr.sr_wait(ctx, victim, 1000)
+        assert e.value.status == sr.SR_ECANCELED
+        assert sr.sr_result(ctx, victim).status == sr.SR_ECANCELED
+        sr.sr_wait(ctx, t0, 120000)
+        assert np.array_equal(out0.numpy(), oracle.warshall(A0.numpy(), 65535).astype(np.uint16))
+        for t, out, want, _ in prods[:-1]:
+            sr.sr_wait(ctx, t, 60000)
+            assert np.array_equal(out.numpy(), want)
+        assert (prods[-1][1].numpy() == 7).all()     # never written
+        with pytest.raises(sr.SemiringError) as e:
+            sr.sr_cancel(ctx, 987654321)
+        assert e.value.status == sr.SR_ENOTFOUND
+        sr.sr_cancel(ctx, t0)                        # finished: no effect
+        assert sr.sr_result(ctx, t0).status == sr.SR_OK
+        st = sr.sr_serve_stats(ctx)
+        assert st["cancelled"] == 1 and st["pending"] == 0 and st["arena_in_use"] == 0
+        for t in [t0, victim] + [p[0] for p in prods[:-1]]:
+            sr.sr_release(ctx, t)
+    finally:
+        sr.sr_destroy(ctx)

@@ -1,0 +1,52 @@
+"""Tracing: every C-ABI call opens an NVTX range in the domain "semiring" and closes
+it on return, failures included.  A small NVTX injection library (tests/native)
+records the events; the calls below fail their argument checks before any CUDA
+call, so no GPU is needed."""
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "native", "nvtx_record.c")
+
+CHILD = r"""
+import ctypes, sys
+from paper_1705_08743_gb300 import _capi as sr
+L = sr.lib
+assert L.antidist_closure(None, None, 4, 4, sr.SR_U8, None) == sr.SR_EINVAL
+assert L.bool_mul(None, 16, 1, 16, 1, 16, 1, 4, 4, 4, sr.SR_BOOL_W32, 0, None) == sr.SR_EINVAL
+assert L.antidist_mul(None, 1, 4, 1, 4, 2, 4, 4, 4, 4, 0, 0, None) == sr.SR_EINVAL
+assert L.sr_cancel(None, 1) == sr.SR_EINVAL
+rec = ctypes.CDLL(sys.argv[1])
+rec.nvtx_record_log.restype = ctypes.c_char_p
+sys.stdout.write(rec.nvtx_record_log().decode())
+"""
+
+
+@pytest.fixture(scope="module")
+def recorder(tmp_path_factory):
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    import __graft_entry__ as g
+    g.build()
+    so = str(tmp_path_factory.mktemp("nvtx") / "libnvtx_record.so")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["gcc", "-shared", "-fPIC", "-O1", "-I", cuda_inc, SRC, "-o", so], check=True)
+    return so
+
+
+def test_entry_points_open_and_close_ranges(recorder):
+    env = dict(os.environ, NVTX_INJECTION64_PATH=recorder, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHILD, recorder], env=env, cwd=ROOT, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [l.split(" ", 2) for l in r.stdout.strip().splitlines()]
+    pushes = [l[2] for l in lines if l[0] == "push"]
+    assert pushes == ["antidist_closure", "bool_mul", "antidist_mul", "sr_cancel"]
+    assert all(l[1] == "semiring" for l in lines)
+    # strictly nested: each push is closed by the next pop, even on the error paths
+    assert [l[0] for l in lines] == ["push", "pop"] * 4
