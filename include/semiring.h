@@ -111,12 +111,16 @@ typedef enum {
                                 Four Russians (8-bit groups of K, 256-entry OR tables of
                                 rows of B; Section 4 names the method for the product):
                                 0 never, 1 for large products (default), 2 always. */
-    SR_OPT_SPIN_LIMIT = 3    /* tries per bounded device-side wait (the tensor-core pipeline's
+    SR_OPT_SPIN_LIMIT = 3,   /* tries per bounded device-side wait (the tensor-core pipeline's
                                 mbarrier waits); a wait that gives up sets the context's status
                                 word, which sr_stream_status reports as SR_ETIMEOUT, and the CTA
                                 drains the copies and MMAs it started and returns.  0 makes
                                 every wait give up at once (fault injection for tests); the
                                 default is sr_config.spin_limit. */
+    SR_OPT_CLOSURE_BLOCK = 4 /* block width of the anti-distance closure's blocked Warshall/Floyd
+                                loop (antidist_closure, dist_closure): 0 automatic (default),
+                                128, 256 or 512.  Wider blocks mean fewer, deeper phase-3
+                                products; their diagonal blocks are closed at width 128. */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 

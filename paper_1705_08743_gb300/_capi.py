@@ -32,6 +32,7 @@ SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD, SR_PEAK_U32_PAI
 SR_OPT_BOOL_TENSOR = 1
 SR_OPT_BOOL_FOUR_RUSSIANS = 2
 SR_OPT_SPIN_LIMIT = 3
+SR_OPT_CLOSURE_BLOCK = 4
 SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 

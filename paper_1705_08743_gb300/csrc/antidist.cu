@@ -1,5 +1,6 @@
-// Anti-distance semiring product and closure (u8: S = 255, u16: S = 65535; the u32
-// kernels, S = 2^32 − 1, are in antidist32.cu and share the closure pipeline here).
+// Anti-distance semiring product and pivot-block kernels (u8: S = 255, u16: S = 65535;
+// the u32 kernels, S = 2^32 − 1, are in antidist32.cu).  The closure schedules that
+// drive them are in closure.cu.
 //
 // Product (Section 2 formula, Section 3 ⊗, Section 4 listings):
 //   C := (accumulate ? C : 0) ⊕ A ⊗ B,   (A ⊗ B)_ij = max_k max(A_ik + B_kj − S, 0).
@@ -10,24 +11,13 @@
 // with its TN entries of row k of B (two 16-bit lanes per register, one DPX
 // add-max per lane pair; see sr_common.cuh for the exact lane arithmetic).
 //
-// Closure (Section 2 Warshall, Section 3 Floyd): three-phase blocked form of
-//   T := A;  for k = 1..D:  T := T ⊕ (T_col k ⊗ T_row k).
-// For each k-block of width PB:
-//   phase 1: T_kk := closure of the diagonal block (PB sequential pivots, one CTA);
-//   phase 2: T_kj := T_kj ⊕ T_kk ⊗ T_kj,  T_ik := T_ik ⊕ T_ik ⊗ T_kk (panels);
-//   phase 3: T_ij := T_ij ⊕ T_ik ⊗ T_kj for all other blocks (the product kernel
-//            with K = PB, panel rows/columns excluded).
-// Every pivot order gives the same fixed point, and rows/columns of the pivot
-// block do not change in their own step, so the blocked order is exact.
-// Phase 1 runs on one CTA (the pivot block closed in registers); phase 2 is two
-// in-place products; a one-block look-ahead overlaps the next pivot's phases 1-2
-// with the current phase 3 (see closure_impl).
+// Pivot block (phase 1 of the blocked closure, Section 2 Warshall / Section 3 Floyd):
+// one CTA closes a 128×128 diagonal block in shared memory and registers, optionally
+// after applying its update from the previous pivot block's panels.
 
 #include <algorithm>
 #include <cstdio>
-#include <mutex>
 #include <type_traits>
-#include <vector>
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
@@ -829,231 +819,14 @@ sr_status launch_antidist_pivot_grouped(const BatchGraph *graphs, const int *act
                        : launch_pivot_grouped_t<KindU16>(graphs, active, n, kb, s);
 }
 
-// Side stream (high priority) and a per-thread pool of events for the look-ahead.
-cudaStream_t side_stream(int i)
-{
-    static cudaStream_t st[kMaxDevices][kSideStreams] = {};
-    static std::mutex mu;
-    const int dev = current_device();
-    std::lock_guard<std::mutex> lk(mu);
-    if (i < 0 || i >= kSideStreams)
-        return nullptr;
-    if (!st[dev][i]) {
-        int lo = 0, hi = 0;
-        cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&st[dev][i], cudaStreamNonBlocking, hi) != cudaSuccess)
-            st[dev][i] = nullptr;
-    }
-    return st[dev][i];
-}
-
-sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
-{
-    static thread_local std::vector<cudaEvent_t> pool[kMaxDevices];
-    std::vector<cudaEvent_t> &p = pool[current_device()];
-    while (p.size() < n) {
-        cudaEvent_t e;
-        SR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        p.push_back(e);
-    }
-    out = &p;
-    return SR_OK;
-}
-
-// Phase 3 of pivot block kb restricted to a set of blocks: rows [r0, r0+nr) and
-// columns [c0, c0+nc) of the matrix, each with one excluded range.
-template <class KD>
-static sr_status phase3(void *T, int64_t ldt, int k0, int bw, int rbeg, int R, int rskip0, int rskipw, int cbeg,
-                        int N, int cskip0, int cskipw, sr_dtype dt, bool vec, cudaStream_t s, int tiles,
-                        int skip_tile = -1)
-{
-    using E = typename KD::elem;
-    E *Te = static_cast<E *>(T);
-    MulArgs a;
-    a.A = Te + (int64_t)rbeg * ldt + k0;                 // column panel: rows from rbeg, columns of block k
-    a.B = Te + (int64_t)k0 * ldt + cbeg;                 // row panel: rows of block k, columns from cbeg
-    a.C = Te + (int64_t)rbeg * ldt + cbeg;
-    a.lda = a.ldb = a.ldc = ldt;
-    a.R = R;
-    a.N = N;
-    a.K = bw;
-    a.accumulate = 1;
-    a.rskip0 = rskip0; a.rskipw = rskipw;
-    a.cskip0 = cskip0; a.cskipw = cskipw;
-    a.skip_tile = skip_tile;
-    return launch_antidist_mul(a, dt, vec, s, tiles);
-}
-
-// Phase 2 of pivot block kb as two in-place products on many CTAs:
-//   row panel    T_kj := T_kj ⊕ T_kk ⊗ T_kj   (B and C are the same panel)
-//   column panel T_ik := T_ik ⊕ T_ik ⊗ T_kk   (A and C are the same panel)
-// with T_kk already closed.  A CTA may read panel entries another CTA has already
-// updated; that is harmless: for any T_kj <= X <= T_kj ⊕ T_kk ⊗ T_kj entrywise,
-// T_kj ⊕ T_kk ⊗ X = T_kj ⊕ T_kk ⊗ T_kj, because T_kk ⊗ T_kk <= T_kk (closed) and
-// ⊗ distributes over ⊕ and is monotone.  Each entry read is either its old or its
-// new value (byte / 16-bit entries are never torn).
-template <class KD>
-static sr_status phase2(void *T, int64_t ldt, int D, int k0, int bw, bool row, sr_dtype dt, bool vec,
-                        cudaStream_t s)
-{
-    using E = typename KD::elem;
-    E *Te = static_cast<E *>(T);
-    if (D - bw <= 0)
-        return SR_OK;
-    MulArgs a;
-    a.lda = a.ldb = a.ldc = ldt;
-    a.K = bw;
-    a.accumulate = 1;
-    a.skip_tile = -1;
-    if (row) {      // rows of block k, all columns but block k
-        a.A = Te + (int64_t)k0 * ldt + k0;
-        a.B = Te + (int64_t)k0 * ldt;
-        a.C = Te + (int64_t)k0 * ldt;
-        a.R = bw; a.N = D - bw;
-        a.rskip0 = 0x7fffffff; a.rskipw = 0;
-        a.cskip0 = k0; a.cskipw = bw;
-    } else {        // all rows but block k, columns of block k
-        a.A = Te + k0;
-        a.B = Te + (int64_t)k0 * ldt + k0;
-        a.C = Te + k0;
-        a.R = D - bw; a.N = bw;
-        a.rskip0 = k0; a.rskipw = bw;
-        a.cskip0 = 0x7fffffff; a.cskipw = 0;
-    }
-    return launch_antidist_mul(a, dt, vec, s, 1);
-}
-
-// Pipelined three-phase blocked closure with a one-block look-ahead (pivot blocks of
-// PB = 128).  The main stream runs phase 3 of pivot block kb on every block outside
-// block rows and columns kb and kb+1; meanwhile three high-priority side streams
-// prepare block kb+1:
-//   P: block (kb+1, kb+1): its update from pivot kb and its closure, on one CTA (phase 1)
-//   R: pivot kb's update of block row kb+1 (outside blocks kb, kb+1), then, once P is
-//      done, the row panel of kb+1 (phase 2)
-//   C: the same for block column kb+1
-// so phases 1 and 2 of the next block run beside phase 3 of this one instead of after
-// it.  The writers are disjoint: main writes outside rows/columns kb, kb+1; R writes
-// block row kb+1, C block column kb+1, P the diagonal block; every one of them reads
-// only panel kb, the diagonal block after P, and its own row or column.  The side work
-// for kb+1 starts once main's phase 3 of kb-1 (the last writer of block row and column
-// kb+1) and the panels of kb are done; main's phase 3 of kb+1 waits for both panels.
-// Fewer blocks than this take the plain two-stream schedule (closure_two_streams):
-// with little phase-3 work per block, the look-ahead's extra launches and events
-// cost more than the panels they hide (GB300: two streams 3% faster at D = 3072,
-// the look-ahead 6% faster at D = 4096).
-constexpr int kLookAheadMinBlocks = 28;
-
-// Two-stream schedule: per pivot block kb, the two panels of kb side by side (row panel
-// on the main stream, column panel on the side stream), then phase 3 of kb on the main
-// stream over every block outside block row and column kb except the diagonal block
-// kb+1, while one CTA on the side stream gives that block its update from pivot kb and
-// closes it (phase 1 of kb+1).
-template <class KD>
-static sr_status closure_two_streams(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s,
-                                     cudaStream_t s2)
-{
-    constexpr int PB = 128;
-    const int nb = (D + PB - 1) / PB;
-    std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
-    for (int kb = 0; kb < nb; ++kb) {
-        const int k0 = kb * PB, bw = std::min(PB, D - k0);
-        const bool next = kb + 1 < nb;
-        cudaEvent_t *e = ev->data() + 4 * kb;
-        SR_CUDA_CHECK(cudaEventRecord(e[0], s));                 // pivot kb closed (main order)
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[0], 0));
-        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s2));
-        SR_CUDA_CHECK(cudaEventRecord(e[1], s2));
-        SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[1], 0));          // both panels done
-        if (!next) {
-            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
-            break;
-        }
-        SR_CUDA_CHECK(cudaEventRecord(e[2], s));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s2, e[2], 0));
-        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, vec, s2)));
-        SR_CUDA_CHECK(cudaEventRecord(e[3], s2));
-        // block (kb+1, kb+1) is logical 128x128 tile (kb, kb) once block row/column kb are removed
-        const int tiles_n = (D - bw + PB - 1) / PB;
-        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0, kb * tiles_n + kb));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(s, e[3], 0));
-    }
-    return SR_OK;
-}
-
-template <class KD>
-static sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaStream_t s)
-{
-    constexpr int PB = 128;
-    constexpr int NONE = 0x7fffffff;
-    const int nb = (D + PB - 1) / PB;
-    auto width = [&](int kb) { return std::min(PB, D - kb * PB); };
-    SR_TRY((launch_pivot<KD, PB>(T, ldt, D, 0, -1, vec, s)));
-    if (nb == 1)
-        return SR_OK;
-    if (nb < kLookAheadMinBlocks && side_stream(0))
-        return closure_two_streams<KD>(T, ldt, D, vec, dt, s, side_stream(0));
-    cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
-    if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
-        for (int kb = 0; kb < nb; ++kb) {
-            const int k0 = kb * PB, bw = width(kb);
-            SR_TRY(phase2<KD>(T, ldt, D, k0, bw, true, dt, vec, s));
-            SR_TRY(phase2<KD>(T, ldt, D, k0, bw, false, dt, vec, s));
-            SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - bw, k0, bw, 0, D - bw, k0, bw, dt, vec, s, 0));
-            if (kb + 1 < nb) SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, -1, vec, s)));
-        }
-        return SR_OK;
-    }
-    std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
-    cudaEvent_t *main_done = ev->data();              // [kb]: main's phase 3 of kb
-    cudaEvent_t *pivot_done = main_done + nb + 1;     // [kb]: block (kb, kb) closed
-    cudaEvent_t *rowp_done = pivot_done + nb + 1;     // [kb]: row panel of kb
-    cudaEvent_t *colp_done = rowp_done + nb + 1;      // [kb]: column panel of kb
-    SR_TRY(phase2<KD>(T, ldt, D, 0, width(0), true, dt, vec, s));
-    SR_TRY(phase2<KD>(T, ldt, D, 0, width(0), false, dt, vec, s));
-    SR_CUDA_CHECK(cudaEventRecord(rowp_done[0], s));
-    SR_CUDA_CHECK(cudaEventRecord(colp_done[0], s));
-    for (int kb = 0; kb < nb; ++kb) {
-        const int k0 = kb * PB, bw = width(kb);
-        const bool next = kb + 1 < nb;
-        const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;     // rows/columns left out
-        if (kb > 0) {
-            SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
-            SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
-        }
-        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - ex, k0, ex, 0, D - ex, k0, ex, dt, vec, s, 0));
-        if (!next)
-            break;
-        SR_CUDA_CHECK(cudaEventRecord(main_done[kb], s));
-        for (cudaStream_t x : {sp, sr_, sc}) {
-            if (kb > 0) SR_CUDA_CHECK(cudaStreamWaitEvent(x, main_done[kb - 1], 0));
-            SR_CUDA_CHECK(cudaStreamWaitEvent(x, rowp_done[kb], 0));
-            SR_CUDA_CHECK(cudaStreamWaitEvent(x, colp_done[kb], 0));
-        }
-        const int k1 = k0 + bw;
-        SR_TRY((launch_pivot<KD, PB>(T, ldt, D, kb + 1, kb, vec, sp)));
-        SR_CUDA_CHECK(cudaEventRecord(pivot_done[kb + 1], sp));
-        SR_TRY(phase3<KD>(T, ldt, k0, bw, k1, bwn, NONE, 0, 0, D - ex, k0, ex, dt, vec, sr_, 1));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(sr_, pivot_done[kb + 1], 0));
-        SR_TRY(phase2<KD>(T, ldt, D, k1, bwn, true, dt, vec, sr_));
-        SR_CUDA_CHECK(cudaEventRecord(rowp_done[kb + 1], sr_));
-        SR_TRY(phase3<KD>(T, ldt, k0, bw, 0, D - ex, k0, ex, k1, bwn, NONE, 0, dt, vec, sc, 1));
-        SR_CUDA_CHECK(cudaStreamWaitEvent(sc, pivot_done[kb + 1], 0));
-        SR_TRY(phase2<KD>(T, ldt, D, k1, bwn, false, dt, vec, sc));
-        SR_CUDA_CHECK(cudaEventRecord(colp_done[kb + 1], sc));
-    }
-    return SR_OK;
-}
-
-sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s)
+sr_status launch_antidist_pivot(void *T, int64_t ldt, int D, int kb, int kprev, sr_dtype dt, bool vec,
+                                cudaStream_t s)
 {
     if (dt == SR_U8)
-        return closure_impl<KindU8>(T, ldt, D, vec, dt, s);
+        return launch_pivot<KindU8, 128>(T, ldt, D, kb, kprev, vec, s);
     if (dt == SR_U32)
-        return closure_impl<KindU32>(T, ldt, D, vec, dt, s);
-    return closure_impl<KindU16>(T, ldt, D, vec, dt, s);
+        return launch_pivot<KindU32, 128>(T, ldt, D, kb, kprev, vec, s);
+    return launch_pivot<KindU16, 128>(T, ldt, D, kb, kprev, vec, s);
 }
 
 // -------------------------------------------------------------------------

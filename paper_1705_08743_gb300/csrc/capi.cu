@@ -198,6 +198,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->spin_limit = value;
         return SR_OK;
     }
+    if (option == SR_OPT_CLOSURE_BLOCK && (value == 0 || value == 128 || value == 256 || value == 512)) {
+        c->closure_width = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -373,7 +377,7 @@ sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64
 }
 
 // ------------------------------------------------------------------ closures
-sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
+sr_status antidist_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
     SR_TRACE("antidist_closure");
     const char *fn = "antidist_closure";
@@ -382,7 +386,7 @@ sr_status antidist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype d
     SR_TRY(check_dim(fn, "D", D));
     SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
     const bool vec = vec_ok(dtype, {{T, ldt}});
-    return launch_antidist_closure(T, ldt, (int)D, dtype, vec, S(stream));
+    return launch_antidist_closure(T, ldt, (int)D, dtype, vec, S(stream), c ? c->closure_width : 0);
 }
 
 sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, int method, void *stream)
@@ -483,7 +487,7 @@ sr_status dist_mul(sr_ctx *c, const void *A, int64_t lda, const void *B, int64_t
     return launch_entrywise(SR_EW_NOT, C, ldc, nullptr, 0, C, ldc, (int)R, (int)N, dtype, s);
 }
 
-sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
+sr_status dist_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
     SR_TRACE("dist_closure");
     const char *fn = "dist_closure";
@@ -494,7 +498,7 @@ sr_status dist_closure(sr_ctx *, void *T, int64_t ldt, int64_t D, sr_dtype dtype
     cudaStream_t s = S(stream);
     // the anti-distance closure of S − T, complemented back (Section 4, De Morgan)
     SR_TRY(launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s));
-    SR_TRY(launch_antidist_closure(T, ldt, (int)D, dtype, vec_ok(dtype, {{T, ldt}}), s));
+    SR_TRY(launch_antidist_closure(T, ldt, (int)D, dtype, vec_ok(dtype, {{T, ldt}}), s, c ? c->closure_width : 0));
     return launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s);
 }
 

@@ -36,7 +36,13 @@ struct MulArgs {
 // tiles: 0 = 128x128 CTA tiles (throughput; u32: 128x64), 1 = 64x64 (latency: more CTAs for
 //        thin panels and small grids)
 sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
-sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s);
+// closure.cu; width: block width of the blocked closure (0 = automatic, 128, 256, 512)
+sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s,
+                                  int width = 0);
+// one CTA closes the 128-wide diagonal block kb of a D×D matrix, after its update from
+// block kprev's panels (kprev < 0: none)
+sr_status launch_antidist_pivot(void *T, int64_t ldt, int D, int kb, int kprev, sr_dtype dt, bool vec,
+                                cudaStream_t s);
 // u32 kernels (antidist32.cu), reached through launch_antidist_mul / launch_antidist_closure
 sr_status launch_antidist32_mul(const MulArgs &a, bool vec, cudaStream_t s, int tiles);
 sr_status launch_antidist32_pivot(void *T, int64_t ldt, int D, int kb, int kprev, cudaStream_t s);

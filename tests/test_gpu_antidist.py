@@ -148,6 +148,51 @@ def test_closure_many_pivot_blocks(dt, D):
         assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
 
 
+_WANT = {}
+
+
+def _warshall_cached(A, S, key):
+    if key not in _WANT:
+        _WANT[key] = oracle.warshall(A, S)
+    return _WANT[key]
+
+
+@pytest.mark.parametrize("dt", DTS)
+@pytest.mark.parametrize("width", [128, 256, 512])
+@pytest.mark.parametrize("D", [100, 300, 777, 1100, 2000])
+def test_closure_block_width(dt, width, D):
+    """Every block width of the blocked closure (SR_OPT_CLOSURE_BLOCK): widths 256 and
+    512 close each diagonal block by a nested 128-wide closure on the pivot side stream
+    and run the look-ahead schedule at any size; one block, ragged last blocks, many
+    blocks."""
+    import paper_1705_08743_gb300 as sr
+    rng = np.random.default_rng(D * 3 + 1)
+    S = S_OF[dt]
+    A = rand_anti(rng, D, D, dt, 2.0 / D, S - S // 10)
+    want = _warshall_cached(A, S, (dt, D))
+    ctx = sr.sr_create()
+    try:
+        sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_BLOCK, width)
+        Td = to_dev(A, 3 if D == 777 else 0)
+        sr.antidist_closure(ctx, Td, Td.shape[1], D, sr_dtype_of(dt))
+        assert np.array_equal(to_host(Td, dt)[:, :D], want)
+    finally:
+        sr.sr_destroy(ctx)
+
+
+def test_closure_block_width_rejects_other_values():
+    import paper_1705_08743_gb300 as sr
+    ctx = sr.sr_create()
+    try:
+        for bad in (-1, 64, 100, 1024):
+            with pytest.raises(sr.SemiringError) as e:
+                sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_BLOCK, bad)
+            assert e.value.status == sr.SR_EINVAL
+        sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_BLOCK, 0)
+    finally:
+        sr.sr_destroy(ctx)
+
+
 @pytest.mark.parametrize("dt", DTS)
 def test_closure_unaligned_ld(dt):
     rng = np.random.default_rng(8)
