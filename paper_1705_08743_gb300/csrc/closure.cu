@@ -57,7 +57,6 @@ sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
 
 namespace {
 
-
 constexpr int PB = 128;               // pivot-kernel block
 constexpr int NONE = 0x7fffffff;      // no excluded range
 
