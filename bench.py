@@ -132,6 +132,16 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workloads
+def measured_bf16_tflops():
+    """Dense bf16 burst throughput measured on the GB300s (MEASURED_PEAKS.json),
+    else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def sha_of(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -588,7 +598,8 @@ class CfgBool:
                                         "seed 2), 32 columns per uint32, word path (Four Russians)")
         else:
             self.D, self.name = 16384, ("bool_closure D=16384 bit-packed uint64: DAG (i<j, p=2/D) union random "
-                                        "digraph (p=1.5/D), seed 2; pack + blocked Warshall")
+                                        "digraph (p=1.5/D), seed 2; pack + blocked Warshall (2048-bit blocks, "
+                                        "panels and phase 3 on the tensor cores)")
         self.ops = float(self.D) ** 3
 
     def host_inputs(self):
@@ -624,6 +635,8 @@ class CfgBool:
         else:
             self.ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, self.dt, D,
                                                                           sr.SR_CLOSURE_SQUARING))
+            self.wctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, self.dt, D,
+                                                                           sr.SR_CLOSURE_WARSHALL))
         self.mul_events = []
 
     def step(self, stream, record_mul=False):
@@ -638,25 +651,33 @@ class CfgBool:
             sr.bool_mul(self.ctx, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
         else:
             sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
-            sr.bool_closure(None, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_WARSHALL, s)
+            sr.bool_closure(self.wctx, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_WARSHALL, s)
         if record_mul:
             e1.record(stream)
             self.mul_events.append((e0, e1))
 
-    def squaring_ms(self, stream, reps=2):
+    def other_forms_ms(self, stream, reps=2):
+        """The same closure by the squaring form and by the 128-bit word schedule (no
+        workspace); bits identical to the step's."""
         import torch
         sr, D, s = self.sr, self.D, stream.cuda_stream
-        ts = []
-        for r in range(reps + 1):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
-            sr.bool_closure(self.ctx, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_SQUARING, s)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r:
-                ts.append(e0.elapsed_time(e1))
-        return min(ts)
+        ref = self.T.clone()
+        out = {}
+        for name, ctx, method in [("squaring", self.ctx, sr.SR_CLOSURE_SQUARING),
+                                  ("warshall_128bit_words", None, sr.SR_CLOSURE_WARSHALL)]:
+            ts = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
+                sr.bool_closure(ctx, self.T, self.nw, D, self.dt, method, s)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(e0.elapsed_time(e1))
+            out[name + "_ms"] = min(ts)
+            out[name + "_identical"] = bool(torch.equal(self.T, ref))
+        return out
 
     def forms_ms(self, stream, reps=3):
         """The same product by each Boolean product kernel: masked OR, Four Russians,
@@ -911,20 +932,30 @@ def run_ours(args, world, rank, local):
         t = sum(mul_ms) / len(mul_ms)
         extra = {"step_us": t * 1e3}
         if wl.kind == "cfg3":
-            extra["squaring_ms"] = wl.squaring_ms(stream)
+            extra.update(wl.other_forms_ms(stream))
         if wl.kind == "prod16k":
             extra["forms_ms"] = wl.forms_ms(stream)
-        kern = {"cfg1": "bool_mul_kernel<32,16,4,4,4> (split K)", "prod16k": "bool_m4r_kernel<8>",
-                "cfg3": "bool_m4r_kernel<8> (closure phase 3, Four Russians) + bool_pivot_kernel<128>"}[wl.kind]
+        kern = {"cfg1": "bool_mul_kernel<32,16,4,4,4> (split K)", "prod16k": "bool_m4r_kernel<8>"}.get(wl.kind)
         achieved = wl.ops / (t * 1e-3) / 1e9
         if wl.kind == "cfg1":            # A, B read and C written once: 3 x 512 x 512 bits
             extra["algorithmic_hbm_gbs"] = 3 * wl.D * wl.D / 8 / (t * 1e-3) / 1e9
-        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": pk_ops / 1e9, "unit": "Gop/s",
-                "frac": achieved / (pk_ops / 1e9),
-                "peak_source": "measured now: issue-bound LOP3 (acc | x & m, 32 columns per instruction) on all SMs"
-                               + ("; the table method needs fewer instructions per op than the masked OR"
-                                  if wl.kind == "prod16k" else ""),
-                "launch_ms": t, "traffic": None}
+        if wl.kind == "cfg3":            # D^3 multiply-adds on the tensor cores: 2 D^3 fp8 flops
+            fp8 = 2.0 * measured_bf16_tflops()
+            tflops = 2.0 * wl.ops / (t * 1e-3) / 1e12
+            roof = {"bound": "tensor", "kernel": "bool_tc_kernel (panels, phase 3 and the diagonal blocks' "
+                                                  "squarings) + operand expansion + bool_mul_kernel",
+                    "achieved": tflops, "peak": fp8, "unit": "TFLOP/s", "frac": tflops / fp8,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured) x 2, the nominal "
+                                   "fp8:bf16 dense ratio",
+                    "launch_ms": t, "traffic": None,
+                    "lop3_equivalent": {"achieved_gops": achieved, "lop3_peak_gops": pk_ops / 1e9}}
+        else:
+            roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": pk_ops / 1e9, "unit": "Gop/s",
+                    "frac": achieved / (pk_ops / 1e9),
+                    "peak_source": "measured now: issue-bound LOP3 (acc | x & m, 32 columns per instruction) on "
+                                   "all SMs" + ("; the table method needs fewer instructions per op than the "
+                                                "masked OR" if wl.kind == "prod16k" else ""),
+                    "launch_ms": t, "traffic": None}
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

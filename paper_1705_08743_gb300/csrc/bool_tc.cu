@@ -48,6 +48,7 @@ struct BoolTcArgs {
     int accumulate;
     int *status;          // nonzero after a bounded wait gave up (may be null)
     uint32_t wait_limit;  // tries per wait before giving up (the context's spin limit)
+    int hole_r0, hole_rn, hole_w0, hole_wn;   // tiles inside this block of C are skipped
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -135,6 +136,11 @@ bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         tn = r / gm;
     }
     const int row0 = tm * tc::BM, ncol0 = tn * tc::BN;
+    if (p.hole_rn > 0) {      // the whole CTA leaves before it touches a barrier or tensor memory
+        const int w0 = ncol0 >> 5, r1 = min(row0 + tc::BM, p.R), w1 = min(w0 + tc::BN / 32, p.ncw);
+        if (row0 >= p.hole_r0 && r1 <= p.hole_r0 + p.hole_rn && w0 >= p.hole_w0 && w1 <= p.hole_w0 + p.hole_wn)
+            return;
+    }
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES), done = smem_u32(bars + 2 * tc::STAGES);
 
     if (tid == 0) {
@@ -339,6 +345,16 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
     if (bool_tc_workspace(a.R, a.K, a.N) > ws_bytes)
         return fail(SR_ENOMEM, "bool_mul (tensor path): workspace too small");
+    if (a.skipw != 0 || a.skipww != 0)
+        return fail(SR_EINVAL, "bool_mul (tensor path): excluded row or word ranges are not supported");
+    if (a.hole_rn > 0) {
+        const bool rows_ok = a.hole_r0 % tc::BM == 0 && ((a.hole_r0 + a.hole_rn) % tc::BM == 0 ||
+                                                         a.hole_r0 + a.hole_rn >= a.R);
+        const bool words_ok = a.hole_w0 % (tc::BN / 32) == 0 &&
+                              ((a.hole_w0 + a.hole_wn) % (tc::BN / 32) == 0 || a.hole_w0 + a.hole_wn >= a.ncw);
+        if (!rows_ok || !words_ok || a.hole_r0 < 0 || a.hole_w0 < 0 || a.hole_wn <= 0)
+            return fail(SR_EINVAL, "bool_mul (tensor path): the untouched block must lie on the 128 x 256 tile grid");
+    }
     uint8_t *Ae = static_cast<uint8_t *>(ws);
     uint8_t *Be = Ae + (int64_t)a.R * Kp;
     Be = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(Be) + 255) & ~uintptr_t(255));
@@ -373,6 +389,7 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     p.accumulate = a.accumulate;
     p.status = status;
     p.wait_limit = (uint32_t)std::max(0, spin_limit);
+    p.hole_r0 = a.hole_r0; p.hole_rn = a.hole_rn; p.hole_w0 = a.hole_w0; p.hole_wn = a.hole_wn;
     p.tiles_n = (a.ncw + tc::BN / 32 - 1) / (tc::BN / 32);
     p.tiles_m = (a.R + tc::BM - 1) / tc::BM;
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;

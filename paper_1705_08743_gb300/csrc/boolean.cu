@@ -471,13 +471,15 @@ static BoolArgs bool_args(const uint32_t *A, const uint32_t *B, uint32_t *C, int
 // overlap of a panel product harmless).
 constexpr int kM4rPhase3MinRows = 2048;
 
-sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
+// One block schedule (128-bit pivot blocks) for the whole D×D matrix of rw words per row;
+// pad bits already clear.  level 0: the one-block look-ahead on side streams 0-2 (events
+// of pool 0); level 1: the same on side streams 3-5 (pool 1), for a closure run inside
+// another one's schedule; without those streams everything runs on s.
+static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s,
+                                      int level)
 {
     constexpr int PB = 128, PW = PB / 32;
     const int nb = (D + PB - 1) / PB;
-    bool_clear_pad_kernel<<<(D + 255) / 256, 256, 0, s>>>(T, ldt, D, D, rw);
-    SR_CUDA_CHECK(cudaGetLastError());
-    count_launches();
     auto pivot = [&](int kb, int kprev, cudaStream_t st) -> sr_status {
         bool_pivot_kernel<PB><<<1, PB, 0, st>>>(T, ldt, D, rw, kb, kprev);
         SR_CUDA_CHECK(cudaGetLastError());
@@ -507,7 +509,8 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
     SR_TRY(pivot(0, -1, s));
     if (nb == 1)
         return SR_OK;
-    cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
+    const int base = level ? 3 : 0;
+    cudaStream_t sp = side_stream(base), sr_ = side_stream(base + 1), sc = side_stream(base + 2);
     if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
         for (int kb = 0; kb < nb; ++kb) {
             const int k0 = kb * PB, bw = width(kb), kw = k0 / 32, wn = word_end(kb, 1) - kw;
@@ -521,7 +524,7 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
         return SR_OK;
     }
     std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev, level));
     cudaEvent_t *main_done = ev->data();
     cudaEvent_t *pivot_done = main_done + nb + 1;
     cudaEvent_t *rowp_done = pivot_done + nb + 1;
@@ -573,6 +576,159 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
         SR_CUDA_CHECK(cudaStreamWaitEvent(sc, pivot_done[kb + 1], 0));
         SR_TRY(launch_bool_mul(col_panel(kb + 1), vec, sc, 1));
         SR_CUDA_CHECK(cudaEventRecord(colp_done[kb + 1], sc));
+    }
+    return SR_OK;
+}
+
+static sr_status bool_clear_pad(uint32_t *T, int64_t ldt, int D, int rw, cudaStream_t s)
+{
+    bool_clear_pad_kernel<<<(D + 255) / 256, 256, 0, s>>>(T, ldt, D, D, rw);
+    SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
+    return SR_OK;
+}
+
+sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
+{
+    SR_TRY(bool_clear_pad(T, ldt, D, rw, s));
+    return bool_closure_blocked(T, ldt, D, rw, vec, s, 0);
+}
+
+// Closure by repeated squaring (Section 2's A ⊗ (I ⊕ A)^(D'-1) identity, D' - 1 rounded up
+// to a power of two): M := I ⊕ A, m squarings, then A ⊗ M, copied back into T.
+size_t bool_squaring_workspace(int64_t D, int64_t rw)
+{
+    const int64_t ldw = (rw + 3) / 4 * 4;
+    return (size_t)(2 * D * ldw * 4) + bool_tc_workspace(D, D, D);
+}
+
+sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes, bool tc,
+                                       int *status, int spin_limit, cudaStream_t s)
+{
+    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words; any
+    // workspace beyond them holds the tensor-core operands when it is large enough
+    const int64_t ldw = ((int64_t)rw + 3) / 4 * 4;
+    const size_t mats = (size_t)(2 * (int64_t)D * ldw * 4);
+    if (mats > ws_bytes)
+        return fail(SR_ENOMEM, "bool_closure: squaring needs at least %zu workspace bytes, context has %zu", mats,
+                    ws_bytes);
+    uint32_t *M = static_cast<uint32_t *>(ws);
+    uint32_t *M2 = M + (int64_t)D * ldw;
+    SR_TRY(launch_copy_rows(T, ldt, M, ldw, D, rw, s));
+    SR_TRY(launch_bool_identity_or(M, ldw, D, s));                       // M = I ⊕ A
+    int m = 0;
+    while (((int64_t)1 << m) < (D - 1 > 1 ? D - 1 : 1)) ++m;
+    void *tcws = static_cast<char *>(ws) + mats;
+    const size_t tcbytes = ws_bytes - mats;
+    const bool tcpath = tc && bool_tc_workspace(D, D, D) <= tcbytes;
+    auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z) -> sr_status {
+        BoolArgs a = bool_args(X, Y, Z, ldw, D, D, D, rw);
+        a.lda = ldx; a.ldb = ldy;
+        a.accumulate = 0;
+        if (tcpath)
+            return launch_bool_mul_tc(a, tcws, tcbytes, status, spin_limit, s);
+        const bool v = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0 &&
+                       ((ldx & 3) == 0) && ((ldy & 3) == 0);
+        return launch_bool_mul(a, v, s);
+    };
+    for (int it = 0; it < m; ++it) {                                      // M := M ⊗ M
+        SR_TRY(mul32(M, ldw, M, ldw, M2));
+        uint32_t *t = M; M = M2; M2 = t;
+    }
+    SR_TRY(mul32(T, ldt, M, ldw, M2));                                    // A ⊗ (I ⊕ A)^(2^m)
+    return launch_copy_rows(M2, ldw, T, ldt, D, rw, s);
+}
+
+// Wide blocks (W = 2048 bits) with phase 3 on the tensor cores.  The tensor-core product
+// costs little per K slice but a fixed amount per launch and output tile (operand
+// expansion, one CTA per 128×256 tile), so deep phase-3 passes pay off (GB300, D = 16384:
+// the product kernel alone in passes of K = 128 / 1024 / 2048 takes 33.8 / 6.4 / 4.4 ms;
+// Four Russians tables with K = 128, the 128-bit schedule's phase 3, 9.2 ms).  Closure
+// times at D = 16384 with W = 1024 / 2048 / 4096: 9.1 / 7.6 / 9.7 ms (wider blocks: fewer
+// passes but a longer chain of diagonal-block work; narrower: shallower passes).  Per block kb:
+//   phase 2: the row panel T_kj := T_kj ⊕ T_kk ⊗ T_kj over every word j and the column
+//            panel over every row i, side by side on the tensor cores (j = k and i = k
+//            change nothing: T_kk ⊗ T_kk <= T_kk once T_kk is closed; the two products
+//            overlap only in T_kk, which neither changes);
+//   phase 3: T := T ⊕ T_col k ⊗ T_row k over the whole matrix except the diagonal block
+//            kb+1 (again the panels themselves do not change), while a side stream gives
+//            block (kb+1, kb+1) its update from kb and closes it by repeated squaring on
+//            the tensor cores (phase 1 of kb+1: log2 W + 1 products of W^3; the 128-bit
+//            Warshall schedule's 16 dependent pivot blocks took 0.74 ms beside phase 3,
+//            longer than phase 3 itself, and the whole closure 8.5 ms instead of 7.6).
+// The operands of every tensor-core product are expanded into the workspace before its
+// kernel runs, so the in-place products read no entry that they write.  Workspace: the
+// main region (phase 3's operands, or the two panels' side by side), then the side
+// region (the squaring's matrices and operands).
+static size_t wide_main_bytes(int64_t D, int W)
+{
+    const size_t panel = bool_tc_workspace(W, W, D);
+    return (std::max(bool_tc_workspace(D, W, D), 2 * panel) + 255) / 256 * 256;
+}
+
+size_t bool_closure_wide_workspace(int64_t D)
+{
+    constexpr int W = kBoolWideBlock;
+    return wide_main_bytes(D, W) + bool_squaring_workspace(W, W / 32 + 2);
+}
+
+sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, bool vec, void *ws, size_t ws_bytes,
+                                   int *status, int spin_limit, cudaStream_t s)
+{
+    constexpr int W = kBoolWideBlock, WW = W / 32;
+    const int nb = (D + W - 1) / W;
+    if (bool_closure_wide_workspace(D) > ws_bytes)
+        return fail(SR_ENOMEM, "bool_closure: the tensor-core schedule needs %zu workspace bytes",
+                    bool_closure_wide_workspace(D));
+    auto width = [&](int kb) { return std::min(W, D - kb * W); };
+    auto words_of = [&](int kb) { return kb + 1 < nb ? WW : rw - kb * WW; };     // the last block runs to rw
+    const size_t main_bytes = wide_main_bytes(D, W), half = main_bytes / 2 / 256 * 256;
+    void *ws_col = static_cast<char *>(ws) + half;
+    void *ws_side = static_cast<char *>(ws) + main_bytes;
+    const size_t side_bytes = ws_bytes - main_bytes;
+    auto close_block = [&](int kb, cudaStream_t st) {
+        const int k0 = kb * W;
+        return launch_bool_closure_squaring(T + (int64_t)k0 * ldt + k0 / 32, ldt, width(kb), words_of(kb), ws_side,
+                                            side_bytes, true, status, spin_limit, st);
+    };
+    SR_TRY(bool_clear_pad(T, ldt, D, rw, s));
+    cudaStream_t sp = side_stream(0), sc = side_stream(1);
+    if (!sp) sp = s;
+    if (!sc) sc = s;
+    std::vector<cudaEvent_t> *ev = nullptr;
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
+    cudaEvent_t *panels_done = ev->data(), *diag_done = panels_done + nb + 1;
+    cudaEvent_t *colp_start = diag_done + nb + 1, *colp_done = colp_start + nb + 1;
+    SR_TRY(close_block(0, s));
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * W, bw = width(kb), kw = k0 / 32, wn = words_of(kb);
+        const bool next = kb + 1 < nb;
+        SR_CUDA_CHECK(cudaEventRecord(colp_start[kb], s));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(sc, colp_start[kb], 0));
+        SR_TRY(launch_bool_mul_tc(bool_args(T + kw, T + (int64_t)k0 * ldt + kw, T + kw, ldt, D, bw, bw, wn), ws_col,
+                                  main_bytes - half, status, spin_limit, sc));                     // column panel
+        SR_CUDA_CHECK(cudaEventRecord(colp_done[kb], sc));
+        SR_TRY(launch_bool_mul_tc(bool_args(T + (int64_t)k0 * ldt + kw, T + (int64_t)k0 * ldt, T + (int64_t)k0 * ldt,
+                                            ldt, bw, bw, D, rw), ws, half, status, spin_limit, s));   // row panel
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
+        const int k1 = k0 + bw, kw1 = k1 / 32;
+        if (next) {
+            const int bwn = width(kb + 1), wn1 = words_of(kb + 1);
+            SR_CUDA_CHECK(cudaEventRecord(panels_done[kb], s));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(sp, panels_done[kb], 0));
+            SR_TRY(launch_bool_mul(bool_args(T + (int64_t)k1 * ldt + kw, T + (int64_t)k0 * ldt + kw1,
+                                             T + (int64_t)k1 * ldt + kw1, ldt, bwn, bw, bwn, wn1), vec, sp));
+            SR_TRY(close_block(kb + 1, sp));
+            SR_CUDA_CHECK(cudaEventRecord(diag_done[kb + 1], sp));
+        }
+        BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D, bw, D, rw);
+        if (next) {
+            p3.hole_r0 = k1; p3.hole_rn = width(kb + 1);
+            p3.hole_w0 = kw1; p3.hole_wn = words_of(kb + 1);
+        }
+        SR_TRY(launch_bool_mul_tc(p3, ws, main_bytes, status, spin_limit, s));
+        if (next)
+            SR_CUDA_CHECK(cudaStreamWaitEvent(s, diag_done[kb + 1], 0));
     }
     return SR_OK;
 }

@@ -211,6 +211,8 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
         return fail(SR_EINVAL, "sr_workspace_query: bytes is NULL");
     *bytes = 0;
     SR_TRY(check_dim("sr_workspace_query", "D", D));
+    if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_WARSHALL && D > kBoolWideBlock)
+        *bytes = bool_closure_wide_workspace(D);                           // tensor-core phase 3
     if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_SQUARING) {
         const int64_t rw = row_units(dtype, D) * u32_per_unit(dtype);
         const int64_t ldw = (rw + 3) / 4 * 4;
@@ -319,6 +321,17 @@ static bool use_tc(const sr_ctx *c, int64_t R, int64_t K, int64_t N, size_t ws_a
     return bool_tc_workspace(R, K, N) <= ws_avail && bool_tc_available();
 }
 
+// Warshall closure with wide blocks and phase 3 on the tensor cores: from D = 8192 by
+// default (fewer blocks leave too little phase-3 work per block to hide the diagonal
+// blocks' closures), whenever there are two blocks or more with SR_OPT_BOOL_TENSOR = 2.
+constexpr int64_t kBoolWideMinD = 8192;
+static bool use_tc_closure(const sr_ctx *c, int64_t D)
+{
+    if (!c || c->bool_tc_mode == 0 || D <= kBoolWideBlock || (c->bool_tc_mode == 1 && D < kBoolWideMinD))
+        return false;
+    return bool_closure_wide_workspace(D) <= c->ws_bytes && bool_tc_available();
+}
+
 // Four Russians tables pay off when its 256-row × 32-word CTAs fill the GPU about
 // 1.5 times over and K spans many 8-bit groups (GB300: 1.3x the masked-OR kernel at
 // 8192^3, 0.64x at 4096^3, where only 64 CTAs exist); smaller products keep the
@@ -401,48 +414,19 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     const int rw = (int)(row_units(dtype, D) * u);
     const bool vec = vec_ok(dtype, {{T, ldt}});
     uint32_t *T32 = static_cast<uint32_t *>(T);
-    if (method == SR_CLOSURE_WARSHALL)
+    if (method == SR_CLOSURE_WARSHALL) {
+        if (use_tc_closure(c, D))
+            return launch_bool_closure_wide(T32, ldt * u, (int)D, rw, vec, c->ws, c->ws_bytes, c->d_status,
+                                            c->spin_limit, S(stream));
         return launch_bool_closure_warshall(T32, ldt * u, (int)D, rw, vec, S(stream));
+    }
     if (method != SR_CLOSURE_SQUARING)
         return fail(SR_EINVAL, "%s: unknown method %d", fn, method);
     if (!c)
         return fail(SR_EINVAL, "%s: the squaring method needs a context with workspace", fn);
-    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words; any
-    // workspace beyond them holds the tensor-core operands when it is large enough
-    const int64_t ldw = ((int64_t)rw + 3) / 4 * 4;
-    if ((size_t)(2 * D * ldw * 4) > c->ws_bytes)
-        return fail(SR_ENOMEM, "%s: squaring needs at least %zu workspace bytes, context has %zu", fn,
-                    (size_t)(2 * D * ldw * 4), c->ws_bytes);
-    uint32_t *M = static_cast<uint32_t *>(c->ws);
-    uint32_t *M2 = M + D * ldw;
-    cudaStream_t s = S(stream);
-    SR_TRY(launch_copy_rows(T32, ldt * u, M, ldw, (int)D, rw, s));
-    SR_TRY(launch_bool_identity_or(M, ldw, (int)D, s));                  // M = I ⊕ A
-    int m = 0;
-    while (((int64_t)1 << m) < (D - 1 > 1 ? D - 1 : 1)) ++m;
-    void *tcws = static_cast<char *>(c->ws) + 2 * D * ldw * 4;
-    const size_t tcbytes = c->ws_bytes - (size_t)(2 * D * ldw * 4);
-    const bool tcpath = use_tc(c, D, D, D, tcbytes);
-    auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z) -> sr_status {
-        BoolArgs a;
-        a.A = X; a.B = Y; a.C = Z;
-        a.lda = ldx; a.ldb = ldy; a.ldc = ldw;
-        a.R = (int)D; a.K = (int)D; a.N = (int)D;
-        a.ncw = rw;
-        a.accumulate = 0;
-        a.skip0 = 0x7fffffff; a.skipw = 0;
-        a.skip0w = 0x7fffffff; a.skipww = 0;
-        if (tcpath)
-            return launch_bool_mul_tc(a, tcws, tcbytes, c->d_status, c->spin_limit, s);
-        const bool v = aligned16(X) && aligned16(Y) && ((ldx & 3) == 0) && ((ldy & 3) == 0);
-        return launch_bool_mul(a, v, s);
-    };
-    for (int it = 0; it < m; ++it) {                                      // M := M ⊗ M
-        SR_TRY(mul32(M, ldw, M, ldw, M2));
-        uint32_t *t = M; M = M2; M2 = t;
-    }
-    SR_TRY(mul32(T32, ldt * u, M, ldw, M2));                              // A ⊗ (I ⊕ A)^(2^m)
-    return launch_copy_rows(M2, ldw, T32, ldt * u, (int)D, rw, s);
+    const bool tc = c->bool_tc_mode != 0 && (c->bool_tc_mode == 2 || D >= 1024) && bool_tc_available();
+    return launch_bool_closure_squaring(T32, ldt * u, (int)D, rw, c->ws, c->ws_bytes, tc, c->d_status, c->spin_limit,
+                                        S(stream));
 }
 
 // ------------------------------------------------------------------ distance form

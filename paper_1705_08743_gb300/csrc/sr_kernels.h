@@ -14,9 +14,10 @@ constexpr int kMaxDevices = 64;
 int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
-constexpr int kSideStreams = 3;
+constexpr int kSideStreams = 6;         // 0-2: a closure's look-ahead; 3-5: that of a closure nested in it
 cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
-sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
+// per-thread, per-device events; level 1 is a second pool for a closure nested in another
+sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out, int level = 0);
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
 // with logical index >= rskip0 are shifted by rskipw, columns of B/C with logical
@@ -62,6 +63,10 @@ struct BoolArgs {
     int skip0, skipw;          // excluded row range (rows of A and C)
     int skip0w, skipww;        // excluded word range (words of B and C)
     int ksplit = 1;            // CTAs along K (set by launch_bool_mul; partial results ORed into C)
+    // tensor-core path only: a block of C left untouched, rows [hole_r0, hole_r0 + hole_rn) x
+    // words [hole_w0, hole_w0 + hole_wn) (hole_rn = 0: none); its edges must fall on the
+    // 128-row x 8-word tile grid or at the end of C
+    int hole_r0 = 0, hole_rn = 0, hole_w0 = 0, hole_wn = 0;
 };
 // shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
 sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape = 0);
@@ -75,6 +80,17 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
 // Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
+// Closure by repeated squaring, A ⊗ (I ⊕ A)^(2^m): ws holds two D×rw word matrices (rows
+// padded to 4 words) and, when tc and room allow, the tensor-core operands of a D^3 product
+size_t bool_squaring_workspace(int64_t D, int64_t rw);
+sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes, bool tc,
+                                       int *status, int spin_limit, cudaStream_t s);
+// Blocked Warshall with kBoolWideBlock-bit blocks and phase 3 on the tensor cores; ws as
+// for launch_bool_mul_tc, at least bool_closure_wide_workspace(D) bytes
+constexpr int kBoolWideBlock = 2048;
+size_t bool_closure_wide_workspace(int64_t D);
+sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, bool vec, void *ws, size_t ws_bytes,
+                                   int *status, int spin_limit, cudaStream_t s);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
                            int rw, int num_sms, cudaStream_t s);
 sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C,

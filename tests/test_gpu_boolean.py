@@ -155,6 +155,25 @@ def test_bool_closure_four_russians_phase3(w, D):
     assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want)
 
 
+@pytest.mark.parametrize("w,D,pad", [(64, 2500, 0), (32, 2333, 3), (64, 4500, 0), (32, 4200, 0)])
+def test_bool_closure_wide_tensor_blocks(w, D, pad):
+    """Warshall form with 2048-bit blocks, panels and phase 3 on the tensor cores (forced
+    below its default size): two and three blocks, ragged last blocks, W32 and W64, an
+    unaligned leading dimension; every word compared with the oracle's packed Warshall."""
+    import paper_1705_08743_gb300 as sr
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    dense = synth.bool_dag_union(D, seed=D + 1)
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, dt, D, sr.SR_CLOSURE_WARSHALL))
+    try:
+        sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 2)
+        got = gpu_bool_closure(dense, w, sr.SR_CLOSURE_WARSHALL, pad=pad, ctx=ctx)
+        sr.sr_stream_status(ctx)
+    finally:
+        sr.sr_destroy(ctx)
+    want = oracle.bool_warshall_w64(oracle.pack_bits(dense))
+    assert np.array_equal(unpacked(got, w, D), unpacked(want, 64, D))
+
+
 def test_bool_closure_pad_and_unaligned(sq_ctx):
     import paper_1705_08743_gb300 as sr
     rng = np.random.default_rng(9)
@@ -205,6 +224,15 @@ def test_cfg3_bool_closure_full_16384(sq_ctx):
     finally:
         sr.sr_destroy(ctx)
     assert np.array_equal(got2, ref)
+    # with a workspace for 2048-deep tensor-core products the Warshall form takes wide blocks
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, sr.SR_BOOL_W64, D,
+                                                              sr.SR_CLOSURE_WARSHALL))
+    try:
+        got3 = gpu_bool_closure(G, 64, sr.SR_CLOSURE_WARSHALL, ctx=ctx)
+        sr.sr_stream_status(ctx)
+    finally:
+        sr.sr_destroy(ctx)
+    assert np.array_equal(got3, ref)
 
 
 # ---------------------------------------------------------------- tensor-core path
