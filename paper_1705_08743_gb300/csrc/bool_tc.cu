@@ -8,15 +8,15 @@
 // rounding a sum of non-negative numbers never reaches 0 from a positive value
 // (below 2^24, fp32 holds the counts exactly anyway).
 //
-// Kernel: one CTA per 128×256 output tile (M = 128, N = 256 per MMA, K = 32 per
-// MMA), 4 warps.  Warp 0 lane 0 streams 128-byte-deep K slices of A (128 rows) and
-// B^T (256 rows) with TMA into a 4-stage shared-memory ring (128-byte swizzle);
-// warp 1 lane 0 issues the MMAs and releases each stage with tcgen05.commit; then
-// all four warps read their 32 accumulator lanes from tensor memory (tcgen05.ld),
-// turn 32 counts into one 32-bit word and OR it into C.  Every wait on an
-// mbarrier is bounded; a wait that gives up sets a status word and the CTA stops
-// issuing work, waits (bounded) for the MMAs it started, frees its tensor memory
-// and returns.
+// Kernel: persistent, one CTA per SM (8 warps), output tiles of 128×256 (M = 128,
+// N = 256 per MMA, K = 32 per MMA).  A producer lane streams 128-byte-deep K slices of A
+// (128 rows) and B^T (256 rows) with TMA into a 4-stage shared-memory ring (128-byte
+// swizzle); an MMA lane issues the MMAs into one of two tensor-memory accumulators and
+// releases each stage with tcgen05.commit; four epilogue warps read their 32 accumulator
+// lanes (tcgen05.ld), turn 32 counts into one 32-bit word and OR it into C while the next
+// tile accumulates in the other buffer.  Every wait on an mbarrier is bounded; a wait that
+// gives up sets a status word and the CTA stops issuing work, waits (bounded) for the
+// copies and MMAs it started, frees its tensor memory and returns.
 
 #include <cuda.h>
 
@@ -32,8 +32,6 @@ namespace tc {
 constexpr int BM = 128, BN = 256, BK = 128;          // BK in bytes = fp8 elements
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK;
-constexpr size_t SMEM = 1024 + (size_t)STAGES * (A_BYTES + B_BYTES) + 128;
-constexpr int TMEM_COLS = 256;
 constexpr uint32_t DRAIN_LIMIT = 1u << 24;    // tries per wait for work already started, on the failure path
 constexpr int GROUP_M = 16;                  // tile rows per rasterisation group
 }  // namespace tc
@@ -111,131 +109,203 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
-bool_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, BoolTcArgs p)
+// Persistent kernel: one CTA per SM walks its tiles (tile t = blockIdx.x + i·gridDim.x in
+// grouped order), the accumulator double-buffered in tensor memory so that the epilogue of
+// one tile overlaps the loads and MMAs of the next (GB300, 16384 × 16384 × K: 2.57 ms for
+// K = 16384 against 2.77 ms with one CTA per tile; eight passes of K = 2048, the Boolean
+// closure's phase-3 shape, 2.56 ms against 4.38 ms).  Warp 0 lane 0 streams K slices
+// through the shared-memory ring (across tile boundaries), warp 1 lane 0 issues the MMAs
+// into accumulator i & 1 for the CTA's i-th tile and commits it to tfull[i & 1], warp 2
+// owns the tensor memory (2 × 256 columns), and warps 4-7 (warp w reads accumulator lanes
+// 32·(w mod 4) ..) turn counts into bits, write C and release the accumulator through
+// tempty[i & 1].  Every wait is bounded; a role that gives up sets the shared failure flag,
+// which the others poll while they wait, and the CTA drains what it started.
+namespace tc {
+constexpr int P_THREADS = 256, EPI_WARP0 = 4;
+constexpr int P_TMEM_COLS = 2 * BN;
+constexpr size_t P_SMEM = 1024 + (size_t)STAGES * (A_BYTES + B_BYTES) + 256;
+}
+
+__device__ __forceinline__ bool mbar_wait_f(uint32_t bar, uint32_t parity, uint32_t limit, const volatile int *failed)
+{
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && *failed) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// tile t of the grid in grouped order (GROUP_M tile rows per group); false for a hole tile
+__device__ __forceinline__ bool tc_tile(const BoolTcArgs &p, int t, int &row0, int &ncol0)
+{
+    const int per_group = tc::GROUP_M * p.tiles_n;
+    const int g = t / per_group, first_m = g * tc::GROUP_M;
+    const int gm = min(tc::GROUP_M, p.tiles_m - first_m);
+    const int r = t - g * per_group;
+    row0 = (first_m + r % gm) * tc::BM;
+    ncol0 = (r / gm) * tc::BN;
+    if (p.hole_rn > 0) {
+        const int w0 = ncol0 >> 5, r1 = min(row0 + tc::BM, p.R), w1 = min(w0 + tc::BN / 32, p.ncw);
+        if (row0 >= p.hole_r0 && r1 <= p.hole_r0 + p.hole_rn && w0 >= p.hole_w0 && w1 <= p.hole_w0 + p.hole_wn)
+            return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(tc::P_THREADS, 1)
+bool_tc_persistent_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, BoolTcArgs p)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;                                              // [STAGES][BM][BK]
     uint8_t *sB = smem + tc::STAGES * tc::A_BYTES;                   // [STAGES][BN][BK]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + tc::STAGES * tc::B_BYTES);  // full[S], empty[S], done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * tc::STAGES + 1);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + tc::STAGES * tc::B_BYTES);
+    // full[S], empty[S], tfull[2], tempty[2], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * tc::STAGES + 5);
     __shared__ int failed;
+    __shared__ uint32_t loads_per_stage[tc::STAGES];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // grouped rasterisation: consecutive CTAs walk GROUP_M tile rows before moving to the
-    // next tile column, so a wave's A and B panels stay resident in L2
-    int tm, tn;
-    {
-        const int b = blockIdx.x, tiles_m = p.tiles_m, tiles_n = p.tiles_n;
-        const int per_group = tc::GROUP_M * tiles_n;
-        const int g = b / per_group, first_m = g * tc::GROUP_M;
-        const int gm = min(tc::GROUP_M, tiles_m - first_m);
-        const int r = b - g * per_group;
-        tm = first_m + r % gm;
-        tn = r / gm;
-    }
-    const int row0 = tm * tc::BM, ncol0 = tn * tc::BN;
-    if (p.hole_rn > 0) {      // the whole CTA leaves before it touches a barrier or tensor memory
-        const int w0 = ncol0 >> 5, r1 = min(row0 + tc::BM, p.R), w1 = min(w0 + tc::BN / 32, p.ncw);
-        if (row0 >= p.hole_r0 && r1 <= p.hole_r0 + p.hole_rn && w0 >= p.hole_w0 && w1 <= p.hole_w0 + p.hole_wn)
-            return;
-    }
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES), done = smem_u32(bars + 2 * tc::STAGES);
+    const int tiles = p.tiles_m * p.tiles_n;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES);
+    const uint32_t tfull0 = smem_u32(bars + 2 * tc::STAGES), tempty0 = smem_u32(bars + 2 * tc::STAGES + 2);
+    const uint32_t done = smem_u32(bars + 2 * tc::STAGES + 4);
+    const volatile int *vfailed = &failed;
 
     if (tid == 0) {
         failed = 0;
         for (int s = 0; s < tc::STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
+            loads_per_stage[s] = 0;
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 4);                      // one arrival per epilogue warp
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     ::"r"(smem_u32(tmem_slot)), "r"(tc::TMEM_COLS) : "memory");
+                     ::"r"(smem_u32(tmem_slot)), "r"(tc::P_TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-
-    // instruction descriptor: f32 accumulate, A = B = e4m3, both K-major, N = 256, M = 128
     const uint32_t idesc = (1u << 4) | ((uint32_t)(tc::BN >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
-    int nload = 0;    // K slices whose TMA loads warp 0 lane 0 issued
 
-    if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < p.nkb; ++kb) {
-            const int s = kb % tc::STAGES;
-            if (kb >= tc::STAGES && !mbar_wait(empty0 + 8 * s, ((kb / tc::STAGES) - 1) & 1, p.wait_limit)) {
-                atomicExch(&failed, 1);
-                break;
+    if (warp == 0 && lane == 0) {                               // TMA producer
+        uint32_t g = 0;
+        for (int t = blockIdx.x; t < tiles && !*vfailed; t += gridDim.x) {
+            int row0, ncol0;
+            if (!tc_tile(p, t, row0, ncol0)) continue;
+            for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+                const int s = (int)(g % tc::STAGES);
+                if (g >= (uint32_t)tc::STAGES &&
+                    !mbar_wait_f(empty0 + 8 * s, ((g / tc::STAGES) - 1) & 1, p.wait_limit, vfailed)) {
+                    atomicExch(&failed, 1);
+                    break;
+                }
+                mbar_expect_tx(full0 + 8 * s, tc::A_BYTES + tc::B_BYTES);
+                tma_load_2d(smem_u32(sA + s * tc::A_BYTES), &tA, kb * tc::BK, row0, full0 + 8 * s);
+                tma_load_2d(smem_u32(sB + s * tc::B_BYTES), &tB, kb * tc::BK, ncol0, full0 + 8 * s);
+                ++loads_per_stage[s];
             }
-            if (*(volatile int *)&failed) break;
-            mbar_expect_tx(full0 + 8 * s, tc::A_BYTES + tc::B_BYTES);
-            tma_load_2d(smem_u32(sA + s * tc::A_BYTES), &tA, kb * tc::BK, row0, full0 + 8 * s);
-            tma_load_2d(smem_u32(sB + s * tc::B_BYTES), &tB, kb * tc::BK, ncol0, full0 + 8 * s);
-            ++nload;
         }
-    } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < p.nkb; ++kb) {
-            const int s = kb % tc::STAGES;
-            if (!mbar_wait(full0 + 8 * s, (kb / tc::STAGES) & 1, p.wait_limit)) {
-                atomicExch(&failed, 1);
+    } else if (warp == 1 && lane == 0) {                        // MMA issuer
+        uint32_t g = 0, i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            int row0, ncol0;
+            if (!tc_tile(p, t, row0, ncol0)) continue;
+            const uint32_t a = i & 1, u = i >> 1;
+            if (u >= 1 && !mbar_wait_f(tempty0 + 8 * a, (u - 1) & 1, p.wait_limit, vfailed)) {
+                ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * tc::A_BYTES), b0 = smem_u32(sB + s * tc::B_BYTES);
+            const uint32_t acc = tmem + a * tc::BN;
+            for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+                const int s = (int)(g % tc::STAGES);
+                if (!mbar_wait_f(full0 + 8 * s, (g / tc::STAGES) & 1, p.wait_limit, vfailed)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + s * tc::A_BYTES), b0 = smem_u32(sB + s * tc::B_BYTES);
 #pragma unroll
-            for (int k4 = 0; k4 < tc::BK / 32; ++k4)
-                umma_f8(tmem, smem_desc(a0 + 32 * k4), smem_desc(b0 + 32 * k4), idesc, (kb | k4) != 0);
-            umma_commit(empty0 + 8 * s);
+                for (int k4 = 0; k4 < tc::BK / 32; ++k4)
+                    umma_f8(acc, smem_desc(a0 + 32 * k4), smem_desc(b0 + 32 * k4), idesc, (kb | k4) != 0);
+                umma_commit(empty0 + 8 * s);
+            }
+            if (!ok) break;
+            umma_commit(tfull0 + 8 * a);
+            ++i;
         }
-        umma_commit(done);          // arrives once every MMA issued above has completed
+        if (!ok) atomicExch(&failed, 1);
+        umma_commit(done);                       // arrives once every MMA issued above has completed
+    } else if (warp >= tc::EPI_WARP0) {                         // epilogue
+        const int q = warp & 3;                                 // accumulator lanes 32q .. 32q + 31
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            int row0, ncol0;
+            if (!tc_tile(p, t, row0, ncol0)) continue;
+            const uint32_t a = i & 1, u = i >> 1;
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait_f(tfull0 + 8 * a, u & 1, p.wait_limit, vfailed) ? 1 : 0;
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(&failed, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int r = row0 + 32 * q + lane;
+#pragma unroll 1
+            for (int c = 0; c < tc::BN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + a * tc::BN + (uint32_t)(32 * c), v);
+                uint32_t word = 0u;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) word |= (v[j] != 0u ? 1u : 0u) << j;
+                const int w = (ncol0 >> 5) + c;
+                if (r < p.R && w < p.ncw) {
+                    const int lo = w * 32;
+                    const uint32_t mask = lo + 32 <= p.N ? 0xFFFFFFFFu : (lo >= p.N ? 0u : (1u << (p.N - lo)) - 1u);
+                    uint32_t *dst = p.C + (int64_t)r * p.ldc + w;
+                    *dst = ((p.accumulate ? *dst : 0u) | word) & mask;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+            ++i;
+        }
     }
     __syncwarp();
-
-    // epilogue: 32 accumulator lanes per warp, 32 columns per tensor-memory load
-    const bool ok = mbar_wait(done, 0, p.wait_limit);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok) atomicExch(&failed, 1);
     __syncthreads();
-    const bool good = !failed;
-    const int r = row0 + 32 * warp + lane;
-#pragma unroll 1
-    for (int c = 0; c < tc::BN / 32; ++c) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);   // whole warp, converged
-        uint32_t word = 0u;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) word |= (v[j] != 0u ? 1u : 0u) << j;
-        const int w = (ncol0 >> 5) + c;
-        if (good && r < p.R && w < p.ncw) {
-            const int lo = w * 32;
-            const uint32_t mask = lo + 32 <= p.N ? 0xFFFFFFFFu : (lo >= p.N ? 0u : (1u << (p.N - lo)) - 1u);
-            uint32_t *dst = p.C + (int64_t)r * p.ldc + w;
-            *dst = ((p.accumulate ? *dst : 0u) | word) & mask;
-        }
+    // drain: every TMA copy this CTA started must land before its shared memory is released,
+    // and every MMA it issued must finish before its tensor memory is freed
+    if (warp == 0 && lane == 0 && failed) {
+        for (int s = 0; s < tc::STAGES; ++s)
+            if (loads_per_stage[s] > 0) mbar_wait(full0 + 8 * s, (loads_per_stage[s] - 1) & 1, tc::DRAIN_LIMIT);
     }
-    if (!good) {
-        if (tid == 0 && p.status) atomicExch(p.status, 1);
-        // drain: every TMA copy this CTA started must land before its shared memory is
-        // released, and every MMA it issued must finish before its tensor memory is freed
-        // (done arrives once they have); these waits have their own, longer, bound
-        if (warp == 0 && lane == 0) {
-            for (int s = 0; s < tc::STAGES && s < nload; ++s) {
-                const int loads = (nload - 1 - s) / tc::STAGES + 1;      // loads issued to stage s
-                mbar_wait(full0 + 8 * s, (loads - 1) & 1, tc::DRAIN_LIMIT);
-            }
-            mbar_wait(done, 0, tc::DRAIN_LIMIT);
-        }
-    }
+    if (warp == 1 && lane == 0) mbar_wait(done, 0, tc::DRAIN_LIMIT);
+    if (tid == 0 && failed && p.status) atomicExch(p.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::TMEM_COLS)
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::P_TMEM_COLS)
                      : "memory");
 }
 
@@ -340,7 +410,7 @@ bool bool_tc_available()
 }
 
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
-                             cudaStream_t s)
+                             cudaStream_t s, int max_ctas)
 {
     const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
     if (bool_tc_workspace(a.R, a.K, a.N) > ws_bytes)
@@ -376,7 +446,8 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     static bool attr[kMaxDevices] = {};
     const int dev = current_device();
     if (!attr[dev]) {
-        SR_CUDA_CHECK(cudaFuncSetAttribute(bool_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
+        SR_CUDA_CHECK(cudaFuncSetAttribute(bool_tc_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc::P_SMEM));
         attr[dev] = true;
     }
     BoolTcArgs p;
@@ -395,7 +466,8 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
     if (tiles > 0x7fffffffLL)
         return fail(SR_EINVAL, "bool_mul (tensor path): too many tiles");
-    bool_tc_kernel<<<(unsigned)tiles, 128, tc::SMEM, s>>>(mA, mB, p);
+    const int64_t grid = std::min<int64_t>(tiles, max_ctas > 0 ? std::min(max_ctas, sms) : sms);
+    bool_tc_persistent_kernel<<<(unsigned)grid, tc::P_THREADS, tc::P_SMEM, s>>>(mA, mB, p);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;

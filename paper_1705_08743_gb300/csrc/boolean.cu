@@ -660,6 +660,10 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
 // kernel runs, so the in-place products read no entry that they write.  Workspace: the
 // main region (phase 3's operands, or the two panels' side by side), then the side
 // region (the squaring's matrices and operands).
+// SMs left to the side stream while phase 3 runs (GB300, D = 16384: 0 / 16 / 32 / 48 SMs
+// left give 6.57 / 6.36 / 6.17 / 6.17 ms: the diagonal chain, not phase 3, sets the pace)
+constexpr int kWideSideSms = 32;
+
 static size_t wide_main_bytes(int64_t D, int W)
 {
     const size_t panel = bool_tc_workspace(W, W, D);
@@ -726,7 +730,9 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, bool
             p3.hole_r0 = k1; p3.hole_rn = width(kb + 1);
             p3.hole_w0 = kw1; p3.hole_wn = words_of(kb + 1);
         }
-        SR_TRY(launch_bool_mul_tc(p3, ws, main_bytes, status, spin_limit, s));
+        // beside the diagonal block's squarings, phase 3 leaves kWideSideSms SMs to them
+        SR_TRY(launch_bool_mul_tc(p3, ws, main_bytes, status, spin_limit, s,
+                                  next ? device_sm_count() - kWideSideSms : 0));
         if (next)
             SR_CUDA_CHECK(cudaStreamWaitEvent(s, diag_done[kb + 1], 0));
     }
