@@ -99,7 +99,9 @@ void sr_destroy(sr_ctx *ctx);
 const char *sr_last_error(void);
 /* Library version string. */
 const char *sr_version(void);
-/* Device workspace bytes a call would need (0 for calls that need none). */
+/* Device workspace bytes for a call on D×D operands (0 for calls that use none): what
+ * SR_CLOSURE_SQUARING and dist_mul need, and what lets bool_mul and the Warshall form of
+ * bool_closure take their tensor-core paths (they run without it). */
 sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size_t *bytes);
 
 /* Options of a context. */
