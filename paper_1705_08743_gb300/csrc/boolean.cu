@@ -471,12 +471,10 @@ static BoolArgs bool_args(const uint32_t *A, const uint32_t *B, uint32_t *C, int
 // overlap of a panel product harmless).
 constexpr int kM4rPhase3MinRows = 2048;
 
-// One block schedule (128-bit pivot blocks) for the whole D×D matrix of rw words per row;
-// pad bits already clear.  level 0: the one-block look-ahead on side streams 0-2 (events
-// of pool 0); level 1: the same on side streams 3-5 (pool 1), for a closure run inside
-// another one's schedule; without those streams everything runs on s.
-static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s,
-                                      int level)
+// Blocked Warshall with 128-bit pivot blocks on the whole D×D matrix of rw words per row
+// (pad bits already clear): the one-block look-ahead on the three side streams when they
+// exist, otherwise everything on s.
+static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
 {
     constexpr int PB = 128, PW = PB / 32;
     const int nb = (D + PB - 1) / PB;
@@ -509,8 +507,7 @@ static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, b
     SR_TRY(pivot(0, -1, s));
     if (nb == 1)
         return SR_OK;
-    const int base = level ? 3 : 0;
-    cudaStream_t sp = side_stream(base), sr_ = side_stream(base + 1), sc = side_stream(base + 2);
+    cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
     if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
         for (int kb = 0; kb < nb; ++kb) {
             const int k0 = kb * PB, bw = width(kb), kw = k0 / 32, wn = word_end(kb, 1) - kw;
@@ -524,7 +521,7 @@ static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, b
         return SR_OK;
     }
     std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev, level));
+    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
     cudaEvent_t *main_done = ev->data();
     cudaEvent_t *pivot_done = main_done + nb + 1;
     cudaEvent_t *rowp_done = pivot_done + nb + 1;
@@ -591,7 +588,7 @@ static sr_status bool_clear_pad(uint32_t *T, int64_t ldt, int D, int rw, cudaStr
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s)
 {
     SR_TRY(bool_clear_pad(T, ldt, D, rw, s));
-    return bool_closure_blocked(T, ldt, D, rw, vec, s, 0);
+    return bool_closure_blocked(T, ldt, D, rw, vec, s);
 }
 
 // Closure by repeated squaring (Section 2's A ⊗ (I ⊕ A)^(D'-1) identity, D' - 1 rounded up

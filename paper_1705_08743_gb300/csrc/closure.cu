@@ -42,10 +42,10 @@ cudaStream_t side_stream(int i)
     return st[dev][i];
 }
 
-sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out, int level)
+sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
 {
-    static thread_local std::vector<cudaEvent_t> pool[2][kMaxDevices];
-    std::vector<cudaEvent_t> &p = pool[level ? 1 : 0][current_device()];
+    static thread_local std::vector<cudaEvent_t> pool[kMaxDevices];
+    std::vector<cudaEvent_t> &p = pool[current_device()];
     while (p.size() < n) {
         cudaEvent_t e;
         SR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

@@ -14,10 +14,9 @@ constexpr int kMaxDevices = 64;
 int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
-constexpr int kSideStreams = 6;         // 0-2: a closure's look-ahead; 3-5: that of a closure nested in it
+constexpr int kSideStreams = 3;
 cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
-// per-thread, per-device events; level 1 is a second pool for a closure nested in another
-sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out, int level = 0);
+sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C
 // with logical index >= rskip0 are shifted by rskipw, columns of B/C with logical
