@@ -236,6 +236,33 @@ def test_cfg3_bool_closure_full_16384(sq_ctx):
 
 
 # ---------------------------------------------------------------- tensor-core path
+@pytest.mark.parametrize("w", [32, 64])
+def test_bool_mul_tensor_path_many_tiles_per_cta(w):
+    """More output tiles (16 x 20) than SMs, so each persistent CTA walks several and
+    alternates its two accumulators; ragged in every dimension, with and without
+    accumulation, against the oracle's packed product."""
+    import paper_1705_08743_gb300 as sr
+    R, K, N = 2000, 1100, 5000
+    rng = np.random.default_rng(2024 + w)
+    dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_MUL, sr.SR_BOOL_W64, max(R, K, N)))
+    sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 2)
+    try:
+        A, B, C0 = rand_bool(rng, R, K, 0.02), rand_bool(rng, K, N, 0.02), rand_bool(rng, R, N, 0.05)
+        Ad, Bd = to_dev(packed(A, w)), to_dev(packed(B, w))
+        for acc in (0, 1):
+            Cd = to_dev(packed(C0, w)) if acc else to_dev(np.zeros_like(packed(C0, w)))
+            sr.bool_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N, dt, acc)
+            sr.sr_stream_status(ctx)
+            got = unpacked(to_host(Cd, np.uint64 if w == 64 else np.uint32), w, N)
+            want = oracle.unpack_bits(oracle.bool_mul_w64(oracle.pack_bits(A), oracle.pack_bits(B), N,
+                                                          C=oracle.pack_bits(C0) if acc else None), N)
+            assert np.array_equal(got, want), acc
+            assert 0.05 < want.mean() < 0.95
+    finally:
+        sr.sr_destroy(ctx)
+
+
 @pytest.mark.parametrize("shape", [(128, 128, 256), (128, 1024, 256), (200, 300, 257), (333, 2100, 700),
                                    (1, 64, 1), (1000, 4096, 1000)])
 @pytest.mark.parametrize("w", [32, 64])
