@@ -177,7 +177,7 @@ sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtyp
  * SR_BOOL_W32/W64).  method SR_CLOSURE_WARSHALL needs no workspace: blocked Warshall
  * with 128-bit pivot blocks.  With a ctx holding sr_workspace_query(SR_OP_BOOL_CLOSURE,
  * .., SR_CLOSURE_WARSHALL) bytes (operands of 2048-deep tensor-core products) and
- * D >= 8192 (any D > 2048 with SR_OPT_BOOL_TENSOR = 2), the loop takes 2048-bit blocks
+ * D >= 4096 (any D > 2048 with SR_OPT_BOOL_TENSOR = 2), the loop takes 2048-bit blocks
  * and runs its panels and phase 3 on the tensor cores (count, then test > 0; the same
  * bits).  SR_CLOSURE_SQUARING needs sr_workspace_query() bytes of ctx workspace. */
 sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,

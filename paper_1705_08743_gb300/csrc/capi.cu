@@ -321,10 +321,11 @@ static bool use_tc(const sr_ctx *c, int64_t R, int64_t K, int64_t N, size_t ws_a
     return bool_tc_workspace(R, K, N) <= ws_avail && bool_tc_available();
 }
 
-// Warshall closure with wide blocks and phase 3 on the tensor cores: from D = 8192 by
-// default (fewer blocks leave too little phase-3 work per block to hide the diagonal
-// blocks' closures), whenever there are two blocks or more with SR_OPT_BOOL_TENSOR = 2.
-constexpr int64_t kBoolWideMinD = 8192;
+// Warshall closure with wide blocks and phase 3 on the tensor cores: from D = 4096 by
+// default (GB300: 0.83 / 1.37 / 2.00 ms at D = 4096 / 6144 / 8192 against 0.86 / 1.72 /
+// 3.07 ms for the 128-bit word schedule), whenever there are two blocks or more with
+// SR_OPT_BOOL_TENSOR = 2.
+constexpr int64_t kBoolWideMinD = 4096;
 static bool use_tc_closure(const sr_ctx *c, int64_t D)
 {
     if (!c || c->bool_tc_mode == 0 || D <= kBoolWideBlock || (c->bool_tc_mode == 1 && D < kBoolWideMinD))
