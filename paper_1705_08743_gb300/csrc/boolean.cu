@@ -717,8 +717,11 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, bool
             const int bwn = width(kb + 1), wn1 = words_of(kb + 1);
             SR_CUDA_CHECK(cudaEventRecord(panels_done[kb], s));
             SR_CUDA_CHECK(cudaStreamWaitEvent(sp, panels_done[kb], 0));
-            SR_TRY(launch_bool_mul(bool_args(T + (int64_t)k1 * ldt + kw, T + (int64_t)k0 * ldt + kw1,
-                                             T + (int64_t)k1 * ldt + kw1, ldt, bwn, bw, bwn, wn1), vec, sp));
+            // its update from kb on the tensor cores too (operands in the squaring's part of
+            // the workspace, which the squaring only takes over after this product)
+            SR_TRY(launch_bool_mul_tc(bool_args(T + (int64_t)k1 * ldt + kw, T + (int64_t)k0 * ldt + kw1,
+                                                T + (int64_t)k1 * ldt + kw1, ldt, bwn, bw, bwn, wn1),
+                                      ws_side, side_bytes, status, spin_limit, sp));
             SR_TRY(close_block(kb + 1, sp));
             SR_CUDA_CHECK(cudaEventRecord(diag_done[kb + 1], sp));
         }
