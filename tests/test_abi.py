@@ -53,3 +53,17 @@ def test_errors_without_device(lib):
     st = lib.lib.bool_mul(None, 16, 1, 16, 1, 16, 1, 4, 4, 4, lib.SR_BOOL_W32, 0, None)
     assert st == lib.SR_EINVAL and "overlap" in lib.last_error()
     assert lib.lib.sr_cancel(None, 1) == lib.SR_EINVAL and "not serving" in lib.last_error()
+
+
+def test_workspace_query_without_device(lib):
+    # host arithmetic only: the Warshall form of bool_closure asks for tensor-core operand
+    # space once it has two 2048-bit blocks, the squaring form always needs its matrices
+    W = lib.SR_CLOSURE_WARSHALL
+    assert lib.sr_workspace_query(lib.SR_OP_BOOL_CLOSURE, lib.SR_BOOL_W64, 2048, W) == 0
+    small = lib.sr_workspace_query(lib.SR_OP_BOOL_CLOSURE, lib.SR_BOOL_W64, 2049, W)
+    big = lib.sr_workspace_query(lib.SR_OP_BOOL_CLOSURE, lib.SR_BOOL_W64, 16384, W)
+    assert 0 < small < big
+    assert 2 * 16384 * 2048 < big < 4 * 16384 * 2048 + (64 << 20)     # phase 3's fp8 operands dominate
+    sq = lib.sr_workspace_query(lib.SR_OP_BOOL_CLOSURE, lib.SR_BOOL_W64, 1000, lib.SR_CLOSURE_SQUARING)
+    assert sq >= 2 * 1000 * 32 * 4
+    assert lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U8, 4096, 0) == 0
