@@ -150,15 +150,17 @@ def sha_of(paths):
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel_key: str, sources):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged since."""
+def load_traffic(kernel_key: str, sources, workload: str):
+    """DRAM bytes per launch from a committed ncu capture of this workload's launch, if the
+    kernel is unchanged since (traffic does not scale with the op count, so a capture at
+    another size does not stand in for this one)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     e = d.get(kernel_key)
-    if not e or e.get("source_sha") != sha_of(sources):
+    if not e or e.get("source_sha") != sha_of(sources) or e.get("bench_workload") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -982,7 +984,7 @@ def run_ours(args, world, rank, local):
                      "unit": "Gop/s", "frac": achieved / peak,
                      "peak_source": "measured now: issue-bound DPX add-max stream on all SMs (sr_peak_probe)",
                      "launch_ms": mul_avg,
-                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources)},
+                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload)},
         "parts_ms": {"product": mul_avg, "closure_and_encode": ms_per_step - mul_avg},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -998,7 +1000,7 @@ def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, la
     p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
     loop_ms = wl.loop_of_single_calls_ms(stream)
     achieved = wl.ops / (ms_per_step * 1e-3) / 1e9
-    traffic = load_traffic(wl.roofline_kernel, wl.roofline_sources)
+    traffic = load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload)
     peak = pk_ops / 1e9
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
