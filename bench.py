@@ -159,8 +159,8 @@ def load_traffic(kernel_key: str, sources, workload: str):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get(kernel_key)
-    if not e or e.get("source_sha") != sha_of(sources) or e.get("bench_workload") != workload:
+    e = d.get(f"{kernel_key} @ {workload}")
+    if not e or e.get("source_sha") != sha_of(sources):
         return None
     return e.get("dram_bytes_per_launch")
 
