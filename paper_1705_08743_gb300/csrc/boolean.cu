@@ -673,7 +673,7 @@ size_t bool_closure_wide_workspace(int64_t D)
     return wide_main_bytes(D, W) + bool_squaring_workspace(W, W / 32 + 2);
 }
 
-sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, bool vec, void *ws, size_t ws_bytes,
+sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes,
                                    int *status, int spin_limit, cudaStream_t s)
 {
     constexpr int W = kBoolWideBlock, WW = W / 32;

@@ -417,7 +417,7 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     uint32_t *T32 = static_cast<uint32_t *>(T);
     if (method == SR_CLOSURE_WARSHALL) {
         if (use_tc_closure(c, D))
-            return launch_bool_closure_wide(T32, ldt * u, (int)D, rw, vec, c->ws, c->ws_bytes, c->d_status,
+            return launch_bool_closure_wide(T32, ldt * u, (int)D, rw, c->ws, c->ws_bytes, c->d_status,
                                             c->spin_limit, S(stream));
         return launch_bool_closure_warshall(T32, ldt * u, (int)D, rw, vec, S(stream));
     }
