@@ -296,18 +296,33 @@ __global__ void __launch_bounds__(PB) bool_panel_kernel(uint32_t *T, int64_t ldt
 // Encoding helpers
 // -------------------------------------------------------------------------
 // one warp per (row, word): lane l reads column 32 w + l, ballot packs the word
-__global__ void bool_pack_kernel(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C, int rw)
+// four bytes -> four bits (byte j nonzero -> bit j)
+__device__ __forceinline__ uint32_t pack_nibble(uint32_t x)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const uint32_t m = __vcmpne4(x, 0u) & 0x01010101u;       // bit 8j = [byte j != 0]
+    return (m | (m >> 7) | (m >> 14) | (m >> 21)) & 0xFu;
+}
+
+// one thread per 32-bit word of M: 32 dense bytes (two 16-byte loads when the row start
+// and leading dimension allow) -> 32 bits, LSB first
+__global__ void bool_pack_kernel(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C, int rw,
+                                 bool vec)
+{
     const int64_t total = (int64_t)R * rw;
-    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; t < total; t += nwarps) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(t / rw), w = (int)(t % rw);
-        const int c = 32 * w + lane;
-        const bool bit = c < C && dense[(int64_t)r * ldd + c] != 0;
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
-        if (lane == 0)
-            M[(int64_t)r * ldm + w] = word;
+        const int c0 = 32 * w;
+        const uint8_t *src = dense + (int64_t)r * ldd + c0;
+        uint32_t word = 0u;
+        if (vec && c0 + 32 <= C) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(src), b = *reinterpret_cast<const uint4 *>(src + 16);
+            word = pack_nibble(a.x) | pack_nibble(a.y) << 4 | pack_nibble(a.z) << 8 | pack_nibble(a.w) << 12 |
+                   pack_nibble(b.x) << 16 | pack_nibble(b.y) << 20 | pack_nibble(b.z) << 24 | pack_nibble(b.w) << 28;
+        } else {
+            for (int j = 0; j < 32 && c0 + j < C; ++j)
+                word |= (src[j] != 0 ? 1u : 0u) << j;
+        }
+        M[(int64_t)r * ldm + w] = word;
     }
 }
 
@@ -743,8 +758,9 @@ sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64
                            int num_sms, cudaStream_t s)
 {
     const int64_t words = (int64_t)R * rw;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 7) / 8, (int64_t)num_sms * 16));
-    bool_pack_kernel<<<blocks, 256, 0, s>>>(dense, ldd, M, ldm, R, C, rw);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms * 16));
+    const bool vec = (reinterpret_cast<uintptr_t>(dense) & 15) == 0 && (ldd & 15) == 0;
+    bool_pack_kernel<<<blocks, 256, 0, s>>>(dense, ldd, M, ldm, R, C, rw, vec);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;

@@ -100,7 +100,7 @@ def test_pack_unpack(w):
     import paper_1705_08743_gb300 as sr
     dt = sr.SR_BOOL_W64 if w == 64 else sr.SR_BOOL_W32
     rng = np.random.default_rng(6)
-    for (R, C) in [(1, 1), (3, 31), (5, 64), (17, 65), (40, 1000)]:
+    for (R, C) in [(1, 1), (3, 31), (5, 64), (17, 65), (40, 1000), (7, 1008), (9, 1024), (3, 4096)]:
         d = rand_bool(rng, R, C, 0.4)
         d[d == 1] = rng.integers(1, 256, size=int(d.sum()))        # any nonzero byte is 1
         dd = to_dev(d)
