@@ -326,12 +326,33 @@ __global__ void bool_pack_kernel(const uint8_t *dense, int64_t ldd, uint32_t *M,
     }
 }
 
-__global__ void bool_unpack_kernel(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C)
+// four bits -> four bytes 0/1 (bit j -> byte j)
+__device__ __forceinline__ uint32_t unpack_nibble(uint32_t n)
 {
-    const int64_t total = (int64_t)R * C;
+    return (n & 1u) | ((n & 2u) << 7) | ((n & 4u) << 14) | ((n & 8u) << 21);
+}
+
+// one thread per 32-bit word of M -> 32 dense bytes (two 16-byte stores when aligned)
+__global__ void bool_unpack_kernel(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C, int rw,
+                                   bool vec)
+{
+    const int64_t total = (int64_t)R * rw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(t / C), c = (int)(t % C);
-        dense[(int64_t)r * ldd + c] = (uint8_t)((M[(int64_t)r * ldm + c / 32] >> (c % 32)) & 1u);
+        const int r = (int)(t / rw), w = (int)(t % rw);
+        const int c0 = 32 * w;
+        if (c0 >= C) continue;
+        const uint32_t word = M[(int64_t)r * ldm + w];
+        uint8_t *dst = dense + (int64_t)r * ldd + c0;
+        if (vec && c0 + 32 <= C) {
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = unpack_nibble((word >> (4 * q)) & 0xFu);
+            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        } else {
+            for (int j = 0; j < 32 && c0 + j < C; ++j)
+                dst[j] = (uint8_t)((word >> j) & 1u);
+        }
     }
 }
 
@@ -769,9 +790,11 @@ sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64
 sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C,
                              int num_sms, cudaStream_t s)
 {
-    const int64_t n = (int64_t)R * C;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
-    bool_unpack_kernel<<<blocks, 256, 0, s>>>(M, ldm, dense, ldd, R, C);
+    const int rw = (C + 31) / 32;
+    const int64_t words = (int64_t)R * rw;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms * 16));
+    const bool vec = (reinterpret_cast<uintptr_t>(dense) & 15) == 0 && (ldd & 15) == 0;
+    bool_unpack_kernel<<<blocks, 256, 0, s>>>(M, ldm, dense, ldd, R, C, rw, vec);
     SR_CUDA_CHECK(cudaGetLastError());
     count_launches();
     return SR_OK;
