@@ -944,8 +944,8 @@ def run_ours(args, world, rank, local):
         if wl.kind == "cfg3":            # D^3 multiply-adds on the tensor cores: 2 D^3 fp8 flops
             fp8 = 2.0 * measured_bf16_tflops()
             tflops = 2.0 * wl.ops / (t * 1e-3) / 1e12
-            roof = {"bound": "tensor", "kernel": "bool_tc_kernel (panels, phase 3 and the diagonal blocks' "
-                                                  "squarings) + operand expansion + bool_mul_kernel",
+            roof = {"bound": "tensor", "kernel": "bool_tc_persistent_kernel (panels, phase 3, the diagonal blocks' "
+                                                  "updates and squarings) + operand expansion + bit packing",
                     "achieved": tflops, "peak": fp8, "unit": "TFLOP/s", "frac": tflops / fp8,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured) x 2, the nominal "
                                    "fp8:bf16 dense ratio",
