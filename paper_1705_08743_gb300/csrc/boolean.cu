@@ -673,12 +673,13 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
 }
 
 // Wide blocks (W = 2048 bits) with phase 3 on the tensor cores.  The tensor-core product
-// costs little per K slice but a fixed amount per launch and output tile (operand
-// expansion, one CTA per 128×256 tile), so deep phase-3 passes pay off (GB300, D = 16384:
-// the product kernel alone in passes of K = 128 / 1024 / 2048 takes 33.8 / 6.4 / 4.4 ms;
-// Four Russians tables with K = 128, the 128-bit schedule's phase 3, 9.2 ms).  Closure
-// times at D = 16384 with W = 1024 / 2048 / 4096: 9.1 / 7.6 / 9.7 ms (wider blocks: fewer
-// passes but a longer chain of diagonal-block work; narrower: shallower passes).  Per block kb:
+// costs little per K slice but a fixed amount per launch (operand expansion, pipeline
+// fill), so deep phase-3 passes pay off (GB300, D = 16384, the earlier one-tile-per-CTA
+// kernel alone in passes of K = 128 / 1024 / 2048: 33.8 / 6.4 / 4.4 ms; the persistent
+// kernel: 3.6 ms for K = 1024, 2.6 ms for K = 2048; Four Russians tables with K = 128, the
+// 128-bit schedule's phase 3, 9.2 ms).  Closure times at D = 16384 with W = 1024 / 2048:
+// 6.9 / 6.2 ms (wider blocks: fewer passes but a longer chain of diagonal-block work;
+// W = 4096 was slower still with the earlier kernel).  Per block kb:
 //   phase 2: the row panel T_kj := T_kj ⊕ T_kk ⊗ T_kj over every word j and the column
 //            panel over every row i, side by side on the tensor cores (j = k and i = k
 //            change nothing: T_kk ⊗ T_kk <= T_kk once T_kk is closed; the two products
@@ -688,11 +689,11 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
 //            block (kb+1, kb+1) its update from kb and closes it by repeated squaring on
 //            the tensor cores (phase 1 of kb+1: log2 W + 1 products of W^3; the 128-bit
 //            Warshall schedule's 16 dependent pivot blocks took 0.74 ms beside phase 3,
-//            longer than phase 3 itself, and the whole closure 8.5 ms instead of 7.6).
+//            longer than phase 3 itself).
 // The operands of every tensor-core product are expanded into the workspace before its
 // kernel runs, so the in-place products read no entry that they write.  Workspace: the
 // main region (phase 3's operands, or the two panels' side by side), then the side
-// region (the squaring's matrices and operands).
+// region (the diagonal update's operands, then the squaring's matrices and operands).
 // SMs left to the side stream while phase 3 runs (GB300, D = 16384: 0 / 16 / 32 / 48 SMs
 // left give 6.57 / 6.36 / 6.17 / 6.17 ms: the diagonal chain, not phase 3, sets the pace)
 constexpr int kWideSideSms = 32;
