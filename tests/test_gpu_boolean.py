@@ -174,6 +174,31 @@ def test_bool_closure_wide_tensor_blocks(w, D, pad):
     assert np.array_equal(unpacked(got, w, D), unpacked(want, 64, D))
 
 
+def test_bool_closure_default_takes_tensor_schedule_from_4096():
+    """With the default options and a context holding the Warshall workspace, D = 4096 and
+    D = 4100 (one ragged block) take the tensor-core schedule; D = 4095 keeps the 128-bit
+    word schedule.  Every word against the oracle, and the kernel launch count tells the
+    schedules apart."""
+    import paper_1705_08743_gb300 as sr
+    launches = {}
+    for D in (4095, 4096, 4100):
+        dense = synth.bool_dag_union(D, seed=D)
+        ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, sr.SR_BOOL_W64, D,
+                                                                  sr.SR_CLOSURE_WARSHALL))
+        try:
+            n0 = sr.sr_kernel_launches()
+            got = gpu_bool_closure(dense, 64, sr.SR_CLOSURE_WARSHALL, ctx=ctx)
+            launches[D] = sr.sr_kernel_launches() - n0
+            sr.sr_stream_status(ctx)
+        finally:
+            sr.sr_destroy(ctx)
+        want = oracle.bool_warshall_w64(oracle.pack_bits(dense))
+        assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want), D
+    # about 100 launches for two 2048-bit blocks (each diagonal block: 12 tensor-core products
+    # with their operand expansions) against about 190 for 32 blocks of 128 bits
+    assert launches[4096] < 0.7 * launches[4095] and launches[4100] < 0.7 * launches[4095], launches
+
+
 def test_bool_closure_pad_and_unaligned(sq_ctx):
     import paper_1705_08743_gb300 as sr
     rng = np.random.default_rng(9)
