@@ -47,6 +47,7 @@ struct BoolTcArgs {
     int *status;          // nonzero after a bounded wait gave up (may be null)
     uint32_t wait_limit;  // tries per wait before giving up (the context's spin limit)
     int hole_r0, hole_rn, hole_w0, hole_wn;   // tiles inside this block of C are skipped
+    const int *run_if;    // device flag: the product is skipped (C untouched) when it reads 0 (may be null)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -173,6 +174,8 @@ bool_tc_persistent_kernel(const __grid_constant__ CUtensorMap tA, const __grid_c
     __shared__ int failed;
     __shared__ uint32_t loads_per_stage[tc::STAGES];
 
+    if (p.run_if && *p.run_if == 0)     // the whole CTA leaves before it touches a barrier or tensor memory
+        return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles = p.tiles_m * p.tiles_n;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + tc::STAGES);
@@ -310,8 +313,10 @@ bool_tc_persistent_kernel(const __grid_constant__ CUtensorMap tA, const __grid_c
 }
 
 // bits -> e4m3 bytes (1.0 = 0x38), rows x Kp, zero past K
-__global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp)
+__global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp,
+                                   const int *run_if)
 {
+    if (run_if && *run_if == 0) return;
     const int64_t total = (int64_t)rows * (Kp / 32);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(t / (Kp / 32)), w = (int)(t % (Kp / 32));
@@ -332,8 +337,10 @@ __global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int
 }
 
 // transpose + expand: out[n][k] = bit (k, n) of M (K rows of bits), rows n < N, zero past K
-__global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp)
+__global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp,
+                                   const int *run_if)
 {
+    if (run_if && *run_if == 0) return;
     const int lane = threadIdx.x & 31;
     const int nwords = (N + 31) / 32, kblocks = Kp / 32;
     const int64_t total = (int64_t)nwords * kblocks;
@@ -410,7 +417,7 @@ bool bool_tc_available()
 }
 
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
-                             cudaStream_t s, int max_ctas)
+                             cudaStream_t s, int max_ctas, const int *run_if)
 {
     const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
     if (bool_tc_workspace(a.R, a.K, a.N) > ws_bytes)
@@ -432,11 +439,11 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     {
         const int64_t n = (int64_t)a.R * (Kp / 32);
         expand_rows_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sms * 16)), 256, 0, s>>>(
-            a.A, a.lda, a.R, a.K, Ae, Kp);
+            a.A, a.lda, a.R, a.K, Ae, Kp, run_if);
         SR_CUDA_CHECK(cudaGetLastError());
         const int64_t nw = (int64_t)((a.N + 31) / 32) * (Kp / 32);
         expand_cols_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((nw + 7) / 8, sms * 16)), 256, 0, s>>>(
-            a.B, a.ldb, a.K, a.N, Be, Kp);
+            a.B, a.ldb, a.K, a.N, Be, Kp, run_if);
         SR_CUDA_CHECK(cudaGetLastError());
         count_launches(2);
     }
@@ -461,6 +468,7 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     p.status = status;
     p.wait_limit = (uint32_t)std::max(0, spin_limit);
     p.hole_r0 = a.hole_r0; p.hole_rn = a.hole_rn; p.hole_w0 = a.hole_w0; p.hole_wn = a.hole_wn;
+    p.run_if = run_if;
     p.tiles_n = (a.ncw + tc::BN / 32 - 1) / (tc::BN / 32);
     p.tiles_m = (a.R + tc::BM - 1) / tc::BM;
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;

@@ -627,25 +627,47 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
     return bool_closure_blocked(T, ldt, D, rw, vec, s);
 }
 
+// *diff := 1 if X and Y (R rows of rw words) differ anywhere (*diff is 0 on entry);
+// clears *clear, the flag the next comparison writes
+__global__ void bool_differs_kernel(const uint32_t *X, const uint32_t *Y, int64_t ld, int R, int rw, int *diff_flag,
+                                    int *clear)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *clear = 0;
+    const int64_t total = (int64_t)R * rw;
+    bool diff = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t off = (t / rw) * ld + t % rw;
+        diff |= X[off] != Y[off];
+    }
+    if (__any_sync(0xFFFFFFFFu, diff) && (threadIdx.x & 31) == 0) *diff_flag = 1;
+}
+
 // Closure by repeated squaring (Section 2's A ⊗ (I ⊕ A)^(D'-1) identity, D' - 1 rounded up
-// to a power of two): M := I ⊕ A, m squarings, then A ⊗ M, copied back into T.
+// to a power of two): M := I ⊕ A, m squarings, then A ⊗ M, copied back into T.  On the
+// tensor-core path the squarings stop early, on the device: once a squaring leaves M
+// unchanged (M ⊗ M = M) every later one would too, so each squaring runs only if the
+// previous one changed M (a flag written by a comparison kernel and read by the next
+// product's kernels when they start; skipped products leave both buffers equal, so the
+// host's buffer swap stays right).  The result is the same bits either way.
 size_t bool_squaring_workspace(int64_t D, int64_t rw)
 {
     const int64_t ldw = (rw + 3) / 4 * 4;
-    return (size_t)(2 * D * ldw * 4) + bool_tc_workspace(D, D, D);
+    return 256 + (size_t)(2 * D * ldw * 4) + bool_tc_workspace(D, D, D);
 }
 
 sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes, bool tc,
                                        int *status, int spin_limit, cudaStream_t s)
 {
-    // M, M2: D rows of rw 32-bit words each, rows padded to a multiple of 4 words; any
-    // workspace beyond them holds the tensor-core operands when it is large enough
+    // flags (256 bytes), then M, M2: D rows of rw 32-bit words each, rows padded to a
+    // multiple of 4 words; any workspace beyond them holds the tensor-core operands when
+    // it is large enough
     const int64_t ldw = ((int64_t)rw + 3) / 4 * 4;
-    const size_t mats = (size_t)(2 * (int64_t)D * ldw * 4);
+    const size_t mats = 256 + (size_t)(2 * (int64_t)D * ldw * 4);
     if (mats > ws_bytes)
         return fail(SR_ENOMEM, "bool_closure: squaring needs at least %zu workspace bytes, context has %zu", mats,
                     ws_bytes);
-    uint32_t *M = static_cast<uint32_t *>(ws);
+    int *flags = static_cast<int *>(ws);
+    uint32_t *M = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
     uint32_t *M2 = M + (int64_t)D * ldw;
     SR_TRY(launch_copy_rows(T, ldt, M, ldw, D, rw, s));
     SR_TRY(launch_bool_identity_or(M, ldw, D, s));                       // M = I ⊕ A
@@ -654,21 +676,32 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
     void *tcws = static_cast<char *>(ws) + mats;
     const size_t tcbytes = ws_bytes - mats;
     const bool tcpath = tc && bool_tc_workspace(D, D, D) <= tcbytes;
-    auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z) -> sr_status {
+    auto mul32 = [&](const uint32_t *X, int64_t ldx, const uint32_t *Y, int64_t ldy, uint32_t *Z,
+                     const int *run_if) -> sr_status {
         BoolArgs a = bool_args(X, Y, Z, ldw, D, D, D, rw);
         a.lda = ldx; a.ldb = ldy;
         a.accumulate = 0;
         if (tcpath)
-            return launch_bool_mul_tc(a, tcws, tcbytes, status, spin_limit, s);
+            return launch_bool_mul_tc(a, tcws, tcbytes, status, spin_limit, s, 0, run_if);
         const bool v = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0 &&
                        ((ldx & 3) == 0) && ((ldy & 3) == 0);
         return launch_bool_mul(a, v, s);
     };
+    if (tcpath)
+        SR_CUDA_CHECK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+    const int64_t words = (int64_t)D * rw;
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, device_sm_count() * 8));
     for (int it = 0; it < m; ++it) {                                      // M := M ⊗ M
-        SR_TRY(mul32(M, ldw, M, ldw, M2));
+        // squaring it runs if squaring it-1 changed M (flag (it-1) mod 2)
+        SR_TRY(mul32(M, ldw, M, ldw, M2, tcpath && it > 0 ? flags + ((it - 1) & 1) : nullptr));
+        if (tcpath) {
+            bool_differs_kernel<<<cblocks, 256, 0, s>>>(M, M2, ldw, D, rw, flags + (it & 1), flags + ((it + 1) & 1));
+            SR_CUDA_CHECK(cudaGetLastError());
+            count_launches();
+        }
         uint32_t *t = M; M = M2; M2 = t;
     }
-    SR_TRY(mul32(T, ldt, M, ldw, M2));                                    // A ⊗ (I ⊕ A)^(2^m)
+    SR_TRY(mul32(T, ldt, M, ldw, M2, nullptr));                           // A ⊗ (I ⊕ A)^(2^m)
     return launch_copy_rows(M2, ldw, T, ldt, D, rw, s);
 }
 

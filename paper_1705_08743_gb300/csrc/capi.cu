@@ -214,9 +214,7 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
     if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_WARSHALL && D > kBoolWideBlock)
         *bytes = bool_closure_wide_workspace(D);                           // tensor-core phase 3
     if (op == SR_OP_BOOL_CLOSURE && is_bool(dtype) && method == SR_CLOSURE_SQUARING) {
-        const int64_t rw = row_units(dtype, D) * u32_per_unit(dtype);
-        const int64_t ldw = (rw + 3) / 4 * 4;
-        *bytes = (size_t)(2 * D * ldw * 4) + bool_tc_workspace(D, D, D);   // squares + tensor-core operands
+        *bytes = bool_squaring_workspace(D, row_units(dtype, D) * u32_per_unit(dtype));   // squares + operands
     }
     if (op == SR_OP_BOOL_MUL && is_bool(dtype))
         *bytes = bool_tc_workspace(D, D, D);

@@ -188,6 +188,12 @@ static int64_t units_of(sr_dtype t, int64_t n)
     return t == SR_BOOL_W32 ? (n + 31) / 32 : t == SR_BOOL_W64 ? (n + 63) / 64 : n;
 }
 static int64_t pad_units(sr_dtype t, int64_t u) { const int per = 16 / es_of(t); return (u + per - 1) / per * per; }
+// workspace of a word-path squaring closure: its flags and the two squares (no tensor-core operands)
+static size_t squaring_bytes(sr_dtype t, int64_t D)
+{
+    const int64_t rw = units_of(t, D) * (t == SR_BOOL_W64 ? 2 : 1);
+    return bool_squaring_workspace(D, rw) - bool_tc_workspace(D, D, D);
+}
 
 // device bytes a request needs (buffers it allocates; resident inputs cost nothing)
 static size_t request_bytes(const sr_request &r)
@@ -198,10 +204,8 @@ static size_t request_bytes(const sr_request &r)
     size_t n = 0;
     if (r.op == SR_OP_ANTIDIST_CLOSURE || r.op == SR_OP_BOOL_CLOSURE) {
         n += mat(r.R, r.R);
-        if (r.op == SR_OP_BOOL_CLOSURE && r.method == SR_CLOSURE_SQUARING) {
-            const int64_t rw = units_of(t, r.R) * (t == SR_BOOL_W64 ? 2 : 1);
-            n += (size_t)(2 * r.R * ((rw + 3) / 4 * 4) * 4 + 256);
-        }
+        if (r.op == SR_OP_BOOL_CLOSURE && r.method == SR_CLOSURE_SQUARING)
+            n += squaring_bytes(t, r.R) + 256;
     } else {
         if (!r.rA) n += mat(r.R, r.K);
         if (!r.rB) n += mat(r.K, r.N);
@@ -285,10 +289,9 @@ static sr_status enqueue_request(ServeState &st, Job &job, cudaStream_t s)
             SR_TRY(launch_antidist_closure(T, ld, (int)D, t, true, s));
         } else if (r.method == SR_CLOSURE_SQUARING) {
             sr_ctx tmp;                                   // workspace = this request's arena block
-            const int64_t rw = units_of(t, D) * u32;
             tmp.ws = dptr(offs[k++]);
-            tmp.ws_bytes = (size_t)(2 * D * ((rw + 3) / 4 * 4) * 4);
-            tmp.bool_tc_mode = 0;                         // the block holds the two squares only
+            tmp.ws_bytes = squaring_bytes(t, D);
+            tmp.bool_tc_mode = 0;                         // the block holds the flags and two squares only
             SR_TRY(bool_closure(&tmp, T, ld, D, t, SR_CLOSURE_SQUARING, s));
         } else {
             SR_TRY(launch_bool_closure_warshall(reinterpret_cast<uint32_t *>(T), ld * u32, (int)D,
@@ -357,10 +360,8 @@ static std::vector<size_t> buffer_sizes(const sr_request &r)
     std::vector<size_t> sizes;
     if (r.op == SR_OP_ANTIDIST_CLOSURE || r.op == SR_OP_BOOL_CLOSURE) {
         sizes.push_back(need(r.R, r.R));
-        if (r.op == SR_OP_BOOL_CLOSURE && r.method == SR_CLOSURE_SQUARING) {
-            const int64_t rw = units_of(t, r.R) * (t == SR_BOOL_W64 ? 2 : 1);
-            sizes.push_back((size_t)(2 * r.R * ((rw + 3) / 4 * 4) * 4));
-        }
+        if (r.op == SR_OP_BOOL_CLOSURE && r.method == SR_CLOSURE_SQUARING)
+            sizes.push_back(squaring_bytes(t, r.R));
     } else {
         if (!r.rA) sizes.push_back(need(r.R, r.K));
         if (!r.rB) sizes.push_back(need(r.K, r.N));

@@ -75,9 +75,10 @@ bool bool_tc_available();
 // spin_limit: tries per bounded wait (0: every wait gives up at once); a wait that gives up
 // sets *status and the CTA drains what it started and returns
 // max_ctas: at most this many CTAs (one per SM; 0 = every SM), leaving the other SMs to
-// work on other streams
+// work on other streams; run_if: a device flag read when the kernels start, the product
+// skipped (C untouched) when it is 0 (null: always run)
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
-                             cudaStream_t s, int max_ctas = 0);
+                             cudaStream_t s, int max_ctas = 0, const int *run_if = nullptr);
 // Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);

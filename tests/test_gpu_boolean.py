@@ -194,9 +194,39 @@ def test_bool_closure_default_takes_tensor_schedule_from_4096():
             sr.sr_destroy(ctx)
         want = oracle.bool_warshall_w64(oracle.pack_bits(dense))
         assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want), D
-    # about 100 launches for two 2048-bit blocks (each diagonal block: 12 tensor-core products
-    # with their operand expansions) against about 190 for 32 blocks of 128 bits
-    assert launches[4096] < 0.7 * launches[4095] and launches[4100] < 0.7 * launches[4095], launches
+    # GB300: 122 launches for two 2048-bit blocks (each diagonal block: 12 tensor-core
+    # products with their operand expansions and 11 convergence checks), 148 with a third,
+    # 4-bit block, against 191 for 32 blocks of 128 bits
+    assert launches[4096] < launches[4095] and launches[4100] < launches[4095], launches
+
+
+@pytest.mark.parametrize("kind", ["chain", "dense", "two_chains"])
+def test_bool_squaring_tensor_path_stops_early_only_when_converged(kind):
+    """Squaring form on the tensor cores, which skips the squarings after the first one that
+    leaves I ⊕ A's power unchanged: a 1500-node chain (every squaring changes it), a dense
+    random graph (converges after a few), and two chains of different lengths (the short one
+    converges first, the long one must not be cut short); every word against the oracle."""
+    import paper_1705_08743_gb300 as sr
+    D = 1500
+    rng = np.random.default_rng(1500)
+    dense = np.zeros((D, D), np.uint8)
+    if kind == "chain":
+        dense[np.arange(D - 1), np.arange(1, D)] = 1
+    elif kind == "dense":
+        dense = rand_bool(rng, D, D, 12.0 / D)
+    else:
+        dense[np.arange(99), np.arange(1, 100)] = 1                     # 0 -> 1 -> ... -> 99
+        dense[np.arange(100, D - 1), np.arange(101, D)] = 1             # 100 -> ... -> 1499
+    ctx = sr.sr_create(workspace_bytes=sr.sr_workspace_query(sr.SR_OP_BOOL_CLOSURE, sr.SR_BOOL_W64, D,
+                                                              sr.SR_CLOSURE_SQUARING))
+    try:
+        sr.sr_set_option(ctx, sr.SR_OPT_BOOL_TENSOR, 2)
+        got = gpu_bool_closure(dense, 64, sr.SR_CLOSURE_SQUARING, ctx=ctx)
+        sr.sr_stream_status(ctx)
+    finally:
+        sr.sr_destroy(ctx)
+    want = oracle.bool_warshall_w64(oracle.pack_bits(dense))
+    assert np.array_equal(np.ascontiguousarray(got).view(np.uint64), want)
 
 
 def test_bool_closure_pad_and_unaligned(sq_ctx):
