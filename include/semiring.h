@@ -179,7 +179,10 @@ sr_status antidist_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtyp
  * .., SR_CLOSURE_WARSHALL) bytes (operands of 2048-deep tensor-core products) and
  * D >= 4096 (any D > 2048 with SR_OPT_BOOL_TENSOR = 2), the loop takes 2048-bit blocks
  * and runs its panels and phase 3 on the tensor cores (count, then test > 0; the same
- * bits).  SR_CLOSURE_SQUARING needs sr_workspace_query() bytes of ctx workspace. */
+ * bits).  SR_CLOSURE_SQUARING (A ⊗ (I ⊕ A)^(2^m), m = ceil(log2(D - 1)); Section 2's
+ * identity) needs sr_workspace_query() bytes of ctx workspace; on the tensor cores
+ * (D >= 1024, or SR_OPT_BOOL_TENSOR = 2) it skips the squarings after the first one that
+ * leaves the power unchanged, which gives the same bits. */
 sr_status bool_closure(sr_ctx *ctx, void *T, int64_t ldt, int64_t D, sr_dtype dtype,
                        int method, void *stream);
 
