@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-8192", action="store_true", help="default workload: skip the D=8192 closure timing")
+    ap.add_argument("--closure", default="auto", choices=["auto", "persistent", "stream"],
+                    help="anti-distance closure schedule (auto: the library's choice with the workspace it asks for)")
     ap.add_argument("--tuning", default="", help="batched workloads: cluster,threshold,ctas_per_sm (skips autotune)")
     ap.add_argument("--only", default="", choices=["", "mul", "closure"],
                     help="profiling aid: run only one part of the step (not a bench line)")
@@ -132,6 +135,26 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workloads
+def closure_ctx(D, sdt, mode="auto"):
+    """A context for the anti-distance closure: its workspace holds what the persistent
+    schedule needs (sr_workspace_query), so the library picks that schedule where it
+    is the automatic choice; mode "persistent" / "stream" forces one schedule."""
+    import paper_1705_08743_gb300 as sr
+    ws = sr.sr_workspace_query(sr.SR_OP_ANTIDIST_CLOSURE, sdt, D) if sdt in (sr.SR_U8, sr.SR_U16) else 0
+    ctx = sr.sr_create(workspace_bytes=ws)
+    sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_PERSISTENT, {"auto": 1, "persistent": 2, "stream": 0}[mode])
+    return ctx
+
+
+def bench_config(wl, world):
+    """The JSON line's `config`: the same dict in both arms (ours and the reference)."""
+    c = {"workload": wl.name, "ops_per_step": wl.ops,
+         "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
+         "parallelism": "replicas" if world > 1 else "single GPU"}
+    c.update(getattr(wl, "config_extra", {}))
+    return c
+
+
 def measured_bf16_tflops():
     """Dense bf16 burst throughput measured on the GB300s (MEASURED_PEAKS.json),
     else the fallback figure."""
@@ -173,6 +196,7 @@ class Cfg2:
         self.name = (f"antidist_closure D={D} {dtype} + antidist_mul {D}x{D}x{D} {dtype} "
                      f"(edge p=0.05, length U{{1..31}}, seed 1; B: stream 3)")
         self.ops = 2 * D ** 3
+        self.config_extra = {"step": "encode x3 + closure (in place) + product"}
 
     def host_inputs(self):
         import numpy as np
@@ -196,10 +220,13 @@ class Cfg2:
         self.B = torch.empty_like(self.T)
         self.C = torch.empty_like(self.T)
         self.mul_events = []
+        self.closure_events = []
+        self.ctx = closure_ctx(D, self.sdt, self.closure_mode)
         sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt)
         sr.antidist_encode(None, self.WB, D, self.B, D, D, D, self.sdt)
 
     only = ""
+    closure_mode = "auto"
 
     def step(self, stream, record_mul=False):
         import torch
@@ -210,13 +237,18 @@ class Cfg2:
             return
         if self.only == "closure":
             sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
-            sr.antidist_closure(None, self.T, D, D, self.sdt, s)
+            sr.antidist_closure(self.ctx, self.T, D, D, self.sdt, s)
             return
         sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
         sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt, s)
         sr.antidist_encode(None, self.WB, D, self.B, D, D, D, self.sdt, s)
-        sr.antidist_closure(None, self.T, D, D, self.sdt, s)
         if record_mul:
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+        sr.antidist_closure(self.ctx, self.T, D, D, self.sdt, s)
+        if record_mul:
+            c1.record(stream)
+            self.closure_events.append((c0, c1))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
         sr.antidist_mul(None, self.A, D, self.B, D, self.C, D, D, D, D, self.sdt, 0, s)
@@ -254,7 +286,7 @@ class Cfg2:
             self.ev[1].record(cs)
         sr.antidist_encode(None, self.WA, D, self.T, D, D, D, self.sdt, s)
         sr.antidist_encode(None, self.WA, D, self.A, D, D, D, self.sdt, s)
-        sr.antidist_closure(None, self.T, D, D, self.sdt, s)
+        sr.antidist_closure(self.ctx, self.T, D, D, self.sdt, s)
         self.ev[2].record(stream)                          # T final
         with torch.cuda.stream(cs):
             cs.wait_event(self.ev[2])
@@ -331,6 +363,7 @@ class Cfg4:
         self.n = n
         self.name = (f"batched antidist_closure: {n} graphs, D log-uniform [32,1024], u16, "
                      f"length U{{1..4000}}, p=8/D, seed 3; one persistent launch")
+        self.config_extra = {"pool": "restored from a device copy before each step, outside the events"}
 
     def host_inputs(self):
         import numpy as np
@@ -824,7 +857,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
-        "config": {"workload": wl.name, "sample": sample["sample"]},
+        "config": bench_config(wl, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -843,6 +876,8 @@ def run_ours(args, world, rank, local):
         run_cfg5(args, wl)
         return
     wl.only = args.only
+    if hasattr(wl, "closure_mode"):
+        wl.closure_mode = args.closure
     if args.tuning:
         wl.fixed_tuning = tuple(int(x) for x in args.tuning.split(","))
     WA, WB = wl.host_inputs()
@@ -878,6 +913,7 @@ def run_ours(args, world, rank, local):
         clocks.start()
         time.sleep(0.3)
     wl.mul_events = []
+    wl.closure_events = []
     barrier(world)
     torch.cuda.synchronize()
     launches0 = sr.sr_kernel_launches()
@@ -962,7 +998,7 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bits", "data": "synthetic",
-            "config": {"workload": wl.name, "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "config": bench_config(wl, world),
             "boolean": extra, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk}), flush=True)
         return
@@ -973,6 +1009,24 @@ def run_ours(args, world, rank, local):
     mul_avg = sum(mul_ms) / len(mul_ms)
     achieved = wl.D ** 3 / (mul_avg * 1e-3) / 1e9
     peak = pk_ops / 1e9
+    sr.sr_stream_status(wl.ctx, stream.cuda_stream)      # no bounded wait of the closure gave up
+    clo_ms = [a.elapsed_time(b) for a, b in wl.closure_events]
+    clo_avg = sum(clo_ms) / len(clo_ms)
+    clo_achieved = wl.D ** 3 / (clo_avg * 1e-3) / 1e9
+    n0 = sr.sr_kernel_launches()
+    with torch.cuda.stream(stream):
+        sr.antidist_closure(wl.ctx, wl.T, wl.D, wl.D, wl.sdt, stream.cuda_stream)
+    torch.cuda.synchronize()
+    persistent = sr.sr_kernel_launches() - n0 == 1
+    roof_closure = {"bound": "alu",
+                    "kernel": (f"antidist_closure_persistent_kernel<Kind{wl.dtype.upper()}> (whole closure, one launch)"
+                               if persistent else "antidist_closure stream schedule (pivot-block kernel, panel and "
+                                                  "phase-3 products)"),
+                    "achieved": clo_achieved, "peak": peak, "unit": "Gop/s", "frac": clo_achieved / peak,
+                    "launch_ms": clo_avg, "timing": "CUDA events around the antidist_closure call, encode excluded"}
+    extra = {}
+    if wl.D == 4096 and wl.dtype == "u8" and not args.no_8192:
+        extra["closure_8192"] = closure_8192(dev, stream, flush, peak, local, args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -984,14 +1038,64 @@ def run_ours(args, world, rank, local):
                      "unit": "Gop/s", "frac": achieved / peak,
                      "peak_source": "measured now: issue-bound DPX add-max stream on all SMs (sr_peak_probe)",
                      "launch_ms": mul_avg,
-                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload)},
-        "parts_ms": {"product": mul_avg, "closure_and_encode": ms_per_step - mul_avg},
+                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload),
+                     "closure": roof_closure},
+        "parts_ms": {"product": mul_avg, "closure": clo_avg, "encode_x3": ms_per_step - mul_avg - clo_avg},
+        "extra": extra,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
+
+
+def closure_8192(dev, stream, flush, peak, local, args, reps=5):
+    """The anti-distance closure at D = 8192 u8 (the config-2 generator at twice the size):
+    `reps` closures timed with CUDA events, each on a fresh copy of the encoded matrix
+    (copied and L2 flushed outside the events), clocks sampled during them."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1705_08743_gb300 as sr
+    D = 8192
+    W = synth.cfg2_antidist(D=D, seed=1, s_edge=0, dtype=np.uint8)
+    Wd = torch.from_numpy(W).to(dev)
+    T0 = torch.empty((D, D), dtype=torch.uint8, device=dev)
+    T = torch.empty_like(T0)
+    s = stream.cuda_stream
+    ctx = closure_ctx(D, sr.SR_U8, args.closure)
+    with torch.cuda.stream(stream):
+        sr.antidist_encode(None, Wd, D, T0, D, D, D, sr.SR_U8, s)
+        for _ in range(2):
+            T.copy_(T0)
+            sr.antidist_closure(ctx, T, D, D, sr.SR_U8, s)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    ev = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            T.copy_(T0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.antidist_closure(ctx, T, D, D, sr.SR_U8, s)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    avg = sum(ms) / len(ms)
+    achieved = D ** 3 / (avg * 1e-3) / 1e9
+    sr.sr_stream_status(ctx, s)          # no bounded wait gave up
+    sr.sr_destroy(ctx)
+    del Wd, T0, T
+    return {"workload": "antidist_closure D=8192 u8 (edge p=0.05, length U{1..31}, seed 1)", "reps": reps,
+            "ms": avg, "ms_min": min(ms), "ms_max": max(ms), "achieved": achieved, "peak": peak, "unit": "Gop/s",
+            "frac": achieved / peak, "clocks": clk}
 
 
 def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, launches, clk, stream):
@@ -1006,9 +1110,9 @@ def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, la
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": {"workload": wl.name, "ops_per_step": wl.ops, "tuning(cluster,coop_threshold,ctas_per_sm)": wl.tuning,
-                   "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write); pool restored outside events"},
-        "batched": {"p50_ms": p50, "p99_ms": p99, "loop_of_single_calls_ms": loop_ms,
+        "config": bench_config(wl, world),
+        "batched": {"tuning(cluster,coop_threshold,ctas_per_sm)": wl.tuning,
+                    "p50_ms": p50, "p99_ms": p99, "loop_of_single_calls_ms": loop_ms,
                     "speedup_vs_loop": loop_ms / ms_per_step},
         "roofline": {"bound": "alu", "kernel": wl.roofline_kernel, "achieved": achieved, "peak": peak,
                      "unit": "Gop/s", "frac": achieved / peak,

@@ -119,12 +119,34 @@ typedef enum {
                                 drains the copies and MMAs it started and returns.  0 makes
                                 every wait give up at once (fault injection for tests); the
                                 default is sr_config.spin_limit. */
-    SR_OPT_CLOSURE_BLOCK = 4 /* block width of the anti-distance closure's blocked Warshall/Floyd
+    SR_OPT_CLOSURE_BLOCK = 4, /* block width of the anti-distance closure's blocked Warshall/Floyd
                                 loop (antidist_closure, dist_closure): 0 automatic (default),
                                 128, 256 or 512.  Wider blocks mean fewer, deeper phase-3
-                                products; their diagonal blocks are closed at width 128. */
+                                products; their diagonal blocks are closed at width 128.
+                                A width other than 0 also turns the persistent schedule off. */
+    SR_OPT_CLOSURE_PERSISTENT = 5, /* u8/u16 anti-distance closure in one persistent launch
+                                (64-wide pivot blocks; work items taken in a dependency order,
+                                each waiting, bounded by SR_OPT_SPIN_LIMIT, on per-block
+                                counters): 0 never, 1 automatic (default; the stream schedule
+                                is faster at every size measured so far), 2 whenever possible.  Needs 16-byte aligned rows, 128 <= D <=
+                                32768 and a ctx workspace of sr_workspace_query(
+                                SR_OP_ANTIDIST_CLOSURE, dtype, D, 0, ..) bytes; without them the
+                                stream schedule runs. */
+    SR_OPT_CLOSURE_PANEL_SHARE = 6 /* persistent closure: share of each pivot block's phase-3
+                                tiles queued before the next pivot block's panels, in 1/256
+                                (0..256, default 128) */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
+
+/* The work order of the persistent anti-distance closure (SR_OPT_CLOSURE_PERSISTENT) for an
+ * order-D matrix and panel share `share` (as SR_OPT_CLOSURE_PANEL_SHARE), for tests and
+ * tools; host only, no CUDA call.  Writes min(cap, count) items to out (host memory, may be
+ * NULL) as 5 ints (type, pivot block s, tile row i, tile column j, second tile column j2
+ * or -1) — type 0: 128x128 phase-3 tiles (i, j) and (i, j2) on the grid without block
+ * row/column s (Section 2 Warshall step, T_ij ⊕= T_is ⊗ T_sj); 1: a row-panel tile j;
+ * 2: a column-panel tile i; 3: the diagonal block s — and returns the item count, or -1
+ * if D is outside [128, 32768]. */
+long long sr_closure_order(int64_t D, int share, int *out, long long cap);
 
 /* ---------------------------------------------------------------- encoding (Sections 3-4) */
 
@@ -324,15 +346,21 @@ sr_status sr_serve_stats(sr_ctx *ctx, sr_serve_stats_t *out);
  * cannot allocate device memory — code that runs where another allocator already owns
  * the device's memory, plugins held to a fixed memory budget, loops that must not pay
  * for cudaMalloc's implicit synchronisation.  Its scratch is a 16 MiB array inside the
- * library image, present on every GPU that loads the library until the process exits.
- *  - T, ldt, D, dtype as in bool_closure; D×D problems whose two scratch matrices
+ * library image; once loaded on a GPU it stays there until the process exits.
+ *  - Loading: with CUDA's default lazy module loading the array is placed on a device
+ *    by the first call on that device (which looks up its address), so that first
+ *    call does take 16 MiB of device memory and may synchronise the device.  Make it
+ *    (a 1×1 matrix will do) before another allocator claims the device's free
+ *    memory, or set CUDA_MODULE_LOADING=EAGER to load it with the CUDA context.
+ *  - T, ldt, D, dtype as in bool_closure (same argument checks); D×D problems whose two scratch matrices
  *    (2·D·ceil32(D)/8 bytes, rows padded to 16 bytes) exceed SR_NOALLOC_SCRATCH_BYTES
  *    return SR_EINVAL before anything is queued; every D <= 8192 fits.
  *  - All calls share the one array and leave their data in it; each call overwrites
  *    the scratch it reads, but calls that overlap on the GPU (unordered streams) race.
  *  - The first call on a device looks the array's address up on that device; make that
  *    first call before any stream capture.
- *  - Calls no cudaMalloc/cudaFree or any allocating routine. */
+ *  - Calls no cudaMalloc/cudaFree or any allocating routine (after the first call on a
+ *    device has loaded the array, as above). */
 sr_status bool_closure_squaring_noalloc(void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream);
 
 /* ---------------------------------------------------------------- distance form (Section 4 dual; Conclusion) */
@@ -384,7 +412,11 @@ typedef enum {
     SR_PEAK_U16_PAIR = 1,    /* max(max(x, na) + nga, acc) on lane pairs (u16): 2 ops per 2 instr */
     SR_PEAK_LOP3 = 2,        /* acc |= x & m (Boolean): 32 ops/instr */
     SR_PEAK_IADD = 3,        /* 32-bit integer add (reference) */
-    SR_PEAK_U32_PAIR = 4     /* max(max(x, na) + pa, acc) on one 32-bit entry (u32): 1 op per 2 instr */
+    SR_PEAK_U32_PAIR = 4,    /* max(max(x, na) + pa, acc) on one 32-bit entry (u32): 1 op per 2 instr */
+    SR_PEAK_TC_F8 = 5        /* tensor cores: tcgen05.mma kind::f8f6f4, M=128 N=256 K=32, e4m3 operands,
+                                f32 accumulators (the Boolean count path's instruction), one CTA per SM
+                                issuing `iters` MMAs; instr = MMAs, ops = flops (2·M·N·K per MMA).
+                                The integer MMA (kind::i8) does not exist for sm_103a. */
 } sr_peak_op;
 sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *stream, double *ms,
                         double *instr_per_s, double *ops_per_s);

@@ -1,8 +1,8 @@
 """GB300 (sm_103a) semiring product and closure library — Python binding.
 
 The computation lives in lib/libsemiring.so (CUDA kernels behind the C ABI of
-include/semiring.h).  This package only marshals arguments: see _capi for the
-one-to-one binding and tensor.py for shape-inferring helpers on torch tensors.
+include/semiring.h).  This package only marshals arguments: _capi is the
+one-to-one binding.
 """
 
 from . import _capi

@@ -28,11 +28,13 @@ SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ETIMEOUT, SR_EAGAIN, SR_EBUSY, SR_ENOT
 SR_BOOL_W32, SR_BOOL_W64, SR_U8, SR_U16, SR_U32 = range(5)
 SR_CLOSURE_WARSHALL, SR_CLOSURE_SQUARING = 0, 1
 SR_OP_ANTIDIST_MUL, SR_OP_BOOL_MUL, SR_OP_ANTIDIST_CLOSURE, SR_OP_BOOL_CLOSURE = range(4)
-SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD, SR_PEAK_U32_PAIR = range(5)
+SR_PEAK_DPX_S16X2, SR_PEAK_U16_PAIR, SR_PEAK_LOP3, SR_PEAK_IADD, SR_PEAK_U32_PAIR, SR_PEAK_TC_F8 = range(6)
 SR_OPT_BOOL_TENSOR = 1
 SR_OPT_BOOL_FOUR_RUSSIANS = 2
 SR_OPT_SPIN_LIMIT = 3
 SR_OPT_CLOSURE_BLOCK = 4
+SR_OPT_CLOSURE_PERSISTENT = 5
+SR_OPT_CLOSURE_PANEL_SHARE = 6
 SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 
@@ -103,6 +105,7 @@ _SIGS = {
     "antidist_closure": (_st, [_vp, _vp, _i64, _i64, _int, _vp]),
     "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
     "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
+    "sr_closure_order": (ctypes.c_longlong, [_i64, _int, _vp, ctypes.c_longlong]),
     "sr_batch_create": (_st, [_vp, ctypes.POINTER(sr_desc), _int, ctypes.POINTER(_vp)]),
     "sr_batch_launch": (_st, [_vp, _int, _vp]),
     "sr_batch_set_tuning": (_st, [_vp, _int, _int, _int]),
@@ -188,6 +191,18 @@ def sr_workspace_query(op: int, dtype: int, D: int, method: int = 0) -> int:
     n = ctypes.c_size_t()
     _check(lib.sr_workspace_query(op, dtype, D, method, ctypes.byref(n)), "sr_workspace_query")
     return n.value
+
+
+def sr_closure_order(D: int, share: int = 128):
+    """The persistent closure's work order: a list of (type, pivot block, tile row, tile
+    column, second tile column or -1); type 0 phase-3 tiles, 1 row-panel tile, 2
+    column-panel tile, 3 diagonal block."""
+    n = lib.sr_closure_order(D, share, None, 0)
+    if n < 0:
+        raise SemiringError(SR_EINVAL, "sr_closure_order", f"D = {D} is outside the persistent schedule's range")
+    buf = (ctypes.c_int * (5 * n))()
+    lib.sr_closure_order(D, share, ctypes.cast(buf, _vp), n)
+    return [tuple(buf[5 * q:5 * q + 5]) for q in range(n)]
 
 
 def sr_stream_status(ctx, stream=None):

@@ -214,7 +214,7 @@ static sr_status launch_mul32_cfg(const MulArgs &a, bool vec, cudaStream_t s)
         return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
     auto kern = vec ? antidist32_mul_kernel<BM, BN, BK, TM, TN, true> : antidist32_mul_kernel<BM, BN, BK, TM, TN, false>;
     static bool attr[2][kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[vec][dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
         attr[vec][dev] = true;
@@ -344,7 +344,7 @@ sr_status launch_antidist32_pivot(void *T, int64_t ldt, int D, int kb, int kprev
     constexpr int PB = 128;
     using Cfg = Pivot32Cfg<PB>;
     static bool attr[kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(antidist32_pivot_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)Cfg::SMEM));

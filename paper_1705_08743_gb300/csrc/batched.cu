@@ -29,6 +29,7 @@
 #include "sr_common.cuh"
 #include "sr_ctx.h"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace cg = cooperative_groups;
 
@@ -442,7 +443,7 @@ static sr_status launch_batched_nc(BatchPlan &p, cudaStream_t s)
     using BT = BatchTile<KD, PB>;
     auto kern = batched_closure_kernel<KD, PB, NC>;
     static bool attr[kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT::SMEM));
         if (NC > 1)
@@ -602,6 +603,7 @@ extern "C" {
 
 sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out)
 {
+    SR_TRACE("sr_batch_create");
     (void)ctx;
     if (!out || !d || n <= 0)
         return fail(SR_EINVAL, "sr_batch_create: need out, descriptors and n > 0");
@@ -610,7 +612,6 @@ sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out)
     if (!b)
         return fail(SR_ENOMEM, "sr_batch_create: host allocation failed");
     BatchPlan &p = b->plan;
-    p.device = current_device();
     p.n = n;
     p.dtype = (sr_dtype)d[0].dtype;
     for (int i = 0; i < n; ++i) {
@@ -646,6 +647,11 @@ sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out)
                 return fail(SR_EINVAL, "sr_batch_create: two graphs of the batch overlap in memory");
             }
     }
+    p.device = current_device();     // after the argument checks, which need no device
+    if (p.device < 0) {
+        delete b;
+        return fail(SR_ECUDA, "sr_batch_create: no current CUDA device with an id below %d", kMaxDevices);
+    }
     p.order.resize(n);
     std::iota(p.order.begin(), p.order.end(), 0);
     std::stable_sort(p.order.begin(), p.order.end(),
@@ -668,6 +674,7 @@ sr_status sr_batch_create(sr_ctx *ctx, const sr_desc *d, int n, sr_batch **out)
 
 sr_status sr_batch_set_tuning(sr_batch *b, int cluster, int coop_threshold, int ctas_per_sm)
 {
+    SR_TRACE("sr_batch_set_tuning");
     if (!b)
         return fail(SR_EINVAL, "sr_batch_set_tuning: NULL batch");
     if ((cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4) || coop_threshold < 1 || ctas_per_sm < 1 ||
@@ -687,6 +694,7 @@ sr_status sr_batch_set_tuning(sr_batch *b, int cluster, int coop_threshold, int 
 
 sr_status sr_batch_get_tuning(const sr_batch *b, int *cluster, int *coop_threshold, int *ctas_per_sm)
 {
+    SR_TRACE("sr_batch_get_tuning");
     if (!b || !cluster || !coop_threshold || !ctas_per_sm)
         return fail(SR_EINVAL, "sr_batch_get_tuning: NULL argument");
     *cluster = b->plan.nc;
@@ -697,6 +705,7 @@ sr_status sr_batch_get_tuning(const sr_batch *b, int *cluster, int *coop_thresho
 
 sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream)
 {
+    SR_TRACE("sr_batch_launch");
     if (!b)
         return fail(SR_EINVAL, "sr_batch_launch: NULL batch");
     BatchPlan &p = b->plan;
@@ -728,6 +737,7 @@ sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream)
 
 sr_status sr_batch_info(const sr_batch *b, int *ngraphs, int *nitems, double *ops)
 {
+    SR_TRACE("sr_batch_info");
     if (!b)
         return fail(SR_EINVAL, "sr_batch_info: NULL batch");
     if (ngraphs) *ngraphs = b->plan.n;
@@ -738,6 +748,7 @@ sr_status sr_batch_info(const sr_batch *b, int *ngraphs, int *nitems, double *op
 
 void sr_batch_destroy(sr_batch *b)
 {
+    SR_TRACE("sr_batch_destroy");
     if (!b)
         return;
     BatchPlan &p = b->plan;
@@ -770,6 +781,7 @@ static std::string batch_signature(const BatchPlan &p)
 
 sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, double *best_ms)
 {
+    SR_TRACE("sr_batch_autotune");
     if (!b)
         return fail(SR_EINVAL, "sr_batch_autotune: NULL batch");
     BatchPlan &p = b->plan;
@@ -825,6 +837,7 @@ sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, do
 
 sr_status sr_batched(sr_ctx *ctx, const sr_desc *d, int n, void *stream)
 {
+    SR_TRACE("sr_batched");
     sr_batch *b = nullptr;
     SR_TRY(sr_batch_create(ctx, d, n, &b));
     sr_status st = SR_OK;

@@ -164,7 +164,7 @@ static sr_status launch_m4r_cfg(const BoolArgs &a, cudaStream_t s)
     if (grid.y > 65535u)
         return fail(SR_EINVAL, "bool_mul: R too large for the tile grid (%d)", a.R);
     static bool attr[kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(bool_m4r_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)SMEM));

@@ -409,9 +409,100 @@ size_t bool_tc_workspace(int64_t R, int64_t K, int64_t N)
     return (size_t)((R + N) * Kp) + 1024;
 }
 
+// Tensor-pipe probe (the roofline denominator of the fp8 count path): one CTA per SM,
+// lane 0 of warp 1 issues `iters` MMAs (kind::f8f6f4, M = 128, N = 256, K = 32, e4m3
+// operands, f32 accumulation — the product kernel's instruction) from shared memory
+// holding 0/1 operands into one tensor-memory accumulator, then commits them to an mbarrier; the
+// CTA frees its tensor memory once they are done.  (The integer MMA, kind::i8, does not
+// exist for sm_103a: ptxas rejects it for that target.)
+__global__ void __launch_bounds__(128, 1) tc_peak_f8_kernel(int iters, int *failed)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // operands like the count path's: e4m3 bytes 1.0 (0x38) or 0, about half of each
+    uint32_t *z = reinterpret_cast<uint32_t *>(smem);
+    for (int i = tid; i < (tc::A_BYTES + tc::B_BYTES) / 4; i += blockDim.x) {
+        const uint32_t h = (uint32_t)i * 0x9E3779B9u;
+        z[i] = ((h >> 7) & 0x01010101u) * 0x38u;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");     // the MMAs read through the async proxy
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(&tmem_slot)), "r"(tc::BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    if (tid == 32) {
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(tc::BN >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
+        const uint64_t ad = smem_desc(smem_u32(smem)), bd = smem_desc(smem_u32(smem + tc::A_BYTES));
+        for (int i = 0; i < iters; ++i) umma_f8(tmem, ad, bd, idesc, i > 0 ? 1u : 0u);
+        umma_commit(smem_u32(&bar));
+        // the MMAs are finite: this wait ends when they do (its bound only guards a fault)
+        if (!mbar_wait(smem_u32(&bar), 0, tc::DRAIN_LIMIT)) atomicExch(failed, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::BN) : "memory");
+}
+
+sr_status peak_tc_f8(int iters, cudaStream_t s, double *ms, double *mma_per_s, double *flops)
+{
+    if (!bool_tc_available())
+        return fail(SR_EINVAL, "sr_peak_probe: no tcgen05 tensor cores on this device");
+    constexpr size_t SMEM = 1024 + (size_t)tc::A_BYTES + tc::B_BYTES;
+    static bool attr[kMaxDevices] = {};
+    SR_DEVICE_SLOT(dev);
+    if (!attr[dev]) {
+        SR_CUDA_CHECK(cudaFuncSetAttribute(tc_peak_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
+        attr[dev] = true;
+    }
+    const int blocks = device_sm_count();
+    int *failed = nullptr;
+    SR_CUDA_CHECK(cudaMallocAsync(&failed, sizeof(int), s));
+    SR_CUDA_CHECK(cudaMemsetAsync(failed, 0, sizeof(int), s));
+    cudaEvent_t e0, e1;
+    SR_CUDA_CHECK(cudaEventCreate(&e0));
+    SR_CUDA_CHECK(cudaEventCreate(&e1));
+    tc_peak_f8_kernel<<<blocks, 128, SMEM, s>>>(std::max(1, iters / 8), failed);     // warm-up
+    SR_CUDA_CHECK(cudaEventRecord(e0, s));
+    tc_peak_f8_kernel<<<blocks, 128, SMEM, s>>>(iters, failed);
+    SR_CUDA_CHECK(cudaEventRecord(e1, s));
+    count_launches(2);
+    SR_CUDA_CHECK(cudaGetLastError());
+    SR_CUDA_CHECK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    int hf = 0;
+    SR_CUDA_CHECK(cudaEventElapsedTime(&t, e0, e1));
+    SR_CUDA_CHECK(cudaMemcpyAsync(&hf, failed, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(failed, s);
+    SR_CUDA_CHECK(cudaStreamSynchronize(s));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (hf)
+        return fail(SR_ETIMEOUT, "sr_peak_probe: the tensor-core probe's completion wait gave up");
+    const double mmas = (double)iters * blocks;
+    *ms = t;
+    *mma_per_s = mmas / (t * 1e-3);
+    *flops = *mma_per_s * 2.0 * tc::BM * tc::BN * 32;
+    return SR_OK;
+}
+
 bool bool_tc_available()
 {
     int dev = current_device(), major = 0;
+    if (dev < 0) return false;
     if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
     return major == 10 && encode_fn() != nullptr;
 }
@@ -451,7 +542,7 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
     if (!make_map(&mA, Ae, a.R, Kp, tc::BM) || !make_map(&mB, Be, a.N, Kp, tc::BN))
         return fail(SR_ECUDA, "bool_mul (tensor path): cannot encode the tensor maps");
     static bool attr[kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(bool_tc_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)tc::P_SMEM));

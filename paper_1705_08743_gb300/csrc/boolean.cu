@@ -392,7 +392,7 @@ static sr_status launch_bool_cfg(const BoolArgs &a, bool vec, cudaStream_t s)
         return fail(SR_EINVAL, "bool_mul: R too large for the tile grid (%d)", a.R);
     auto kern = vec ? bool_mul_kernel<BM, BNW, BKW, TM, TNW, true> : bool_mul_kernel<BM, BNW, BKW, TM, TNW, false>;
     static bool attr[2][kMaxDevices] = {};
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);
     if (!attr[vec][dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
         attr[vec][dev] = true;

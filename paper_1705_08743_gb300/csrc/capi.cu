@@ -50,14 +50,21 @@ void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order
 int current_device()
 {
     int d = 0;
-    if (cudaGetDevice(&d) != cudaSuccess) d = 0;
-    return d < 0 ? 0 : (d >= kMaxDevices ? kMaxDevices - 1 : d);
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return (d < 0 || d >= kMaxDevices) ? -1 : d;
 }
 
 int device_sm_count()
 {
     static int cache[kMaxDevices] = {};
     const int d = current_device();
+    if (d < 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 1;
+        return n;
+    }
     if (cache[d] == 0) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 1;
@@ -79,15 +86,15 @@ static int64_t row_units(sr_dtype t, int64_t n)
 }
 static int u32_per_unit(sr_dtype t) { return t == SR_BOOL_W64 ? 2 : 1; }
 
-static sr_status check_dim(const char *fn, const char *name, int64_t v)
+sr_status check_dim(const char *fn, const char *name, int64_t v)
 {
     if (v <= 0 || v > 0x7fffffffLL)
         return fail(SR_EINVAL, "%s: %s = %lld must be in [1, 2^31)", fn, name, (long long)v);
     return SR_OK;
 }
 
-static sr_status check_mat(const char *fn, const char *name, const void *p, int64_t ld, int64_t rows,
-                           int64_t cols, sr_dtype t)
+sr_status check_mat(const char *fn, const char *name, const void *p, int64_t ld, int64_t rows, int64_t cols,
+                    sr_dtype t)
 {
     if (!p)
         return fail(SR_EINVAL, "%s: %s is NULL", fn, name);
@@ -131,6 +138,11 @@ extern "C" {
 
 const char *sr_last_error(void) { return g_err.c_str(); }
 
+long long sr_closure_order(int64_t D, int share, int *out, long long cap)
+{
+    return antidist_closure_persistent_order(D, share, out, cap);
+}
+
 const char *sr_version(void) { return "semiring-gb300 0.1 (sm_103a)"; }
 
 uint64_t sr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -144,6 +156,10 @@ sr_status sr_create(sr_ctx **out, const sr_config *cfg)
     if (!c)
         return fail(SR_ENOMEM, "sr_create: host allocation failed");
     c->device = current_device();
+    if (c->device < 0) {
+        delete c;
+        return fail(SR_ECUDA, "sr_create: no current CUDA device with an id below %d", kMaxDevices);
+    }
     if (cfg) {
         c->ws_bytes = cfg->workspace_bytes;
         c->spin_limit = cfg->spin_limit > 0 ? cfg->spin_limit : kDefaultSpinLimit;
@@ -202,6 +218,14 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->closure_width = value;
         return SR_OK;
     }
+    if (option == SR_OPT_CLOSURE_PERSISTENT && value >= 0 && value <= 2) {
+        c->closure_persistent = value;
+        return SR_OK;
+    }
+    if (option == SR_OPT_CLOSURE_PANEL_SHARE && value >= 0 && value <= 256) {
+        c->closure_share = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -218,6 +242,8 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
     }
     if (op == SR_OP_BOOL_MUL && is_bool(dtype))
         *bytes = bool_tc_workspace(D, D, D);
+    if (op == SR_OP_ANTIDIST_CLOSURE && (dtype == SR_U8 || dtype == SR_U16))
+        *bytes = antidist_closure_persistent_workspace(D);                 // persistent schedule
     if (op == SR_OP_DIST_MUL && is_anti(dtype))
         *bytes = (size_t)(2 * D * ((D + 15) / 16 * 16) * esize(dtype) + 1024);
     return SR_OK;
@@ -389,6 +415,24 @@ sr_status bool_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64
 }
 
 // ------------------------------------------------------------------ closures
+// D from which the persistent schedule is the automatic choice (u8, u16)
+static int64_t persistent_min_d(sr_dtype t) { return t == SR_U8 ? kPersistentAutoMinU8 : kPersistentAutoMinU16; }
+
+// The anti-distance closure of T in place: the persistent schedule where the context
+// allows it and holds its workspace, the stream schedules of closure.cu otherwise.
+static sr_status closure_dispatch(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, bool vec,
+                                  cudaStream_t s)
+{
+    if (c && vec && c->closure_width == 0 && c->closure_persistent > 0 && (dtype == SR_U8 || dtype == SR_U16) &&
+        (c->closure_persistent == 2 || D >= persistent_min_d(dtype))) {
+        const size_t need = antidist_closure_persistent_workspace(D);
+        if (need > 0 && c->ws && c->ws_bytes >= need)
+            return launch_antidist_closure_persistent(T, ldt, (int)D, dtype, c->ws, c->ws_bytes, c->d_status,
+                                                      c->spin_limit, c->closure_share, s);
+    }
+    return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, c ? c->closure_width : 0);
+}
+
 sr_status antidist_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
     SR_TRACE("antidist_closure");
@@ -398,7 +442,7 @@ sr_status antidist_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype 
     SR_TRY(check_dim(fn, "D", D));
     SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));
     const bool vec = vec_ok(dtype, {{T, ldt}});
-    return launch_antidist_closure(T, ldt, (int)D, dtype, vec, S(stream), c ? c->closure_width : 0);
+    return closure_dispatch(c, T, ldt, D, dtype, vec, S(stream));
 }
 
 sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, int method, void *stream)
@@ -481,7 +525,7 @@ sr_status dist_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     cudaStream_t s = S(stream);
     // the anti-distance closure of S − T, complemented back (Section 4, De Morgan)
     SR_TRY(launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s));
-    SR_TRY(launch_antidist_closure(T, ldt, (int)D, dtype, vec_ok(dtype, {{T, ldt}}), s, c ? c->closure_width : 0));
+    SR_TRY(closure_dispatch(c, T, ldt, D, dtype, vec_ok(dtype, {{T, ldt}}), s));
     return launch_entrywise(SR_EW_NOT, T, ldt, nullptr, 0, T, ldt, (int)D, (int)D, dtype, s);
 }
 

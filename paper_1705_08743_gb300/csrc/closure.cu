@@ -31,7 +31,7 @@ cudaStream_t side_stream(int i)
     static std::mutex mu;
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(mu);
-    if (i < 0 || i >= kSideStreams)
+    if (dev < 0 || i < 0 || i >= kSideStreams)
         return nullptr;
     if (!st[dev][i]) {
         int lo = 0, hi = 0;
@@ -45,7 +45,8 @@ cudaStream_t side_stream(int i)
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out)
 {
     static thread_local std::vector<cudaEvent_t> pool[kMaxDevices];
-    std::vector<cudaEvent_t> &p = pool[current_device()];
+    SR_DEVICE_SLOT(dev);
+    std::vector<cudaEvent_t> &p = pool[dev];
     while (p.size() < n) {
         cudaEvent_t e;
         SR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

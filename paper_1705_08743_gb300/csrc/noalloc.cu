@@ -21,11 +21,20 @@
 //  - The first call on a device looks up the array's device address on that
 //    device (cudaGetSymbolAddress, once per device); make that first call
 //    before any stream capture.
+//  - The library is built without relocatable device code, so this file is a
+//    module of its own, and with CUDA's default lazy module loading the module
+//    (and with it the 16 MiB array) is loaded onto a device only by that first
+//    address lookup.  So the first call on each device does reserve the array's
+//    memory there and may synchronise the device; a caller whose allocator will
+//    later own all free memory makes that first call (e.g. on a 1×1 matrix)
+//    before the allocator reserves it, or sets CUDA_MODULE_LOADING=EAGER so that
+//    every module is loaded when the CUDA context is created.
 
 #include <mutex>
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace sr {
 
@@ -43,7 +52,7 @@ static void *g_noalloc_ptr[kMaxDevices] = {};
 // Device address of the scratch array on the current device, looked up once per device.
 static sr_status scratch_ptr(uint32_t **out)
 {
-    const int dev = current_device();
+    SR_DEVICE_SLOT(dev);   // fails rather than share another device's cached address
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
@@ -64,18 +73,14 @@ using namespace sr;
 
 extern "C" sr_status bool_closure_squaring_noalloc(void *T, int64_t ldt, int64_t D, sr_dtype dtype, void *stream)
 {
+    SR_TRACE("bool_closure_squaring_noalloc");
     const char *fn = "bool_closure_squaring_noalloc";
     if (dtype != SR_BOOL_W32 && dtype != SR_BOOL_W64)
         return fail(SR_EINVAL, "%s: dtype must be SR_BOOL_W32 or SR_BOOL_W64", fn);
-    if (D <= 0 || D > 0x7fffffffLL)
-        return fail(SR_EINVAL, "%s: D = %lld must be in [1, 2^31)", fn, (long long)D);
-    if (!T)
-        return fail(SR_EINVAL, "%s: T is NULL", fn);
+    SR_TRY(check_dim(fn, "D", D));
+    SR_TRY(check_mat(fn, "T", T, ldt, D, D, dtype));               // same bounds as bool_closure
     const int u = dtype == SR_BOOL_W64 ? 2 : 1;                  // 32-bit words per word of dtype
     const int64_t units = dtype == SR_BOOL_W64 ? (D + 63) / 64 : (D + 31) / 32;
-    if (ldt < units)
-        return fail(SR_EINVAL, "%s: ldt (%lld) is below the row width (%lld words)", fn, (long long)ldt,
-                    (long long)units);
     const int64_t rw = units * u;                                 // 32-bit words per row
     const int64_t ldw = (rw + 3) / 4 * 4;                         // scratch rows padded to 16 bytes
     const int64_t need = 2 * D * ldw * (int64_t)sizeof(uint32_t);

@@ -65,11 +65,13 @@ extern "C" sr_status sr_peak_probe(int op, int iters, int blocks_per_sm, void *s
 {
     if (!ms || !instr_per_s || !ops_per_s)
         return fail(SR_EINVAL, "sr_peak_probe: NULL output");
-    if (op < SR_PEAK_DPX_S16X2 || op > SR_PEAK_U32_PAIR)
+    if (op < SR_PEAK_DPX_S16X2 || op > SR_PEAK_TC_F8)
         return fail(SR_EINVAL, "sr_peak_probe: unknown op %d", op);
     if (iters <= 0 || blocks_per_sm <= 0 || blocks_per_sm > 64)
         return fail(SR_EINVAL, "sr_peak_probe: iters > 0 and 1 <= blocks_per_sm <= 64");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (op == SR_PEAK_TC_F8)            // one CTA per SM; blocks_per_sm does not apply
+        return peak_tc_f8(iters, s, ms, instr_per_s, ops_per_s);
     const int blocks = device_sm_count() * blocks_per_sm, threads = 256;
     uint32_t *sink = nullptr;
     SR_CUDA_CHECK(cudaMallocAsync(&sink, threads * sizeof(uint32_t), s));

@@ -565,6 +565,10 @@ sr_status sr_serve_start(sr_ctx *c, const sr_serve_config *cfg)
         return fail(SR_ENOMEM, "sr_serve_start: host allocation failed");
     st->cfg = k;
     st->device = current_device();
+    if (st->device < 0) {
+        delete st;
+        return fail(SR_ECUDA, "sr_serve_start: no current CUDA device with an id below %d", kMaxDevices);
+    }
     cudaError_t e = cudaMalloc(&st->base, k.arena_bytes);
     if (e != cudaSuccess) {
         delete st;

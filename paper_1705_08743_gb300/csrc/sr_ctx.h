@@ -24,6 +24,8 @@ struct sr_ctx {
     int bool_tc_mode = 1;         // tensor-core Boolean products: 0 never, 1 when K >= 1024, 2 when possible
     int bool_m4r_mode = 1;        // Four Russians Boolean products: 0 never, 1 large products, 2 always
     int closure_width = 0;        // anti-distance closure block width: 0 automatic, 128, 256, 512
+    int closure_persistent = 1;   // persistent closure: 0 never, 1 large D, 2 whenever possible
+    int closure_share = 128;      // persistent closure: phase-3 share before the next panels (/256)
     sr::ServeState *serve = nullptr;
     std::map<std::string, std::array<int, 3>> tune;   // autotuned batch configurations by signature
 };

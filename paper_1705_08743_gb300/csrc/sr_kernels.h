@@ -11,9 +11,24 @@
 namespace sr {
 
 constexpr int kMaxDevices = 64;
-int current_device();          // cudaGetDevice, clamped to [0, kMaxDevices)
+int current_device();          // cudaGetDevice; -1 if that fails or the id is >= kMaxDevices
+// Declares `const int var` = the current device id; returns SR_ECUDA from the
+// enclosing function when there is no usable device id (per-device tables here
+// have kMaxDevices slots, and a clamped id would name another device's entry).
+#define SR_DEVICE_SLOT(var)                                                              \
+    const int var = ::sr::current_device();                                              \
+    if (var < 0)                                                                         \
+        return ::sr::fail(SR_ECUDA, "no current CUDA device with an id below %d", ::sr::kMaxDevices)
 int device_sm_count();         // SMs of the current device (cached)
 void count_launches(int n = 1); // launch counter behind sr_kernel_launches()
+// Argument checks shared by the entry points (capi.cu): a dimension in [1, 2^31);
+// a non-null matrix of `rows` rows whose leading dimension covers `cols` entries
+// (Boolean: words) and whose extent stays below 2^46 units.  SR_EINVAL otherwise.
+sr_status check_dim(const char *fn, const char *name, int64_t v);
+sr_status check_mat(const char *fn, const char *name, const void *p, int64_t ld, int64_t rows, int64_t cols,
+                    sr_dtype t);
+// bool_tc.cu: fp8 tensor-pipe probe (tcgen05 kind::f8f6f4, 128x256x32 MMAs); flops = 2·M·N·K per MMA
+sr_status peak_tc_f8(int iters, cudaStream_t s, double *ms, double *mma_per_s, double *flops);
 constexpr int kSideStreams = 3;
 cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
@@ -36,6 +51,20 @@ struct MulArgs {
 // tiles: 0 = 128x128 CTA tiles (throughput; u32: 128x64), 1 = 64x64 (latency: more CTAs for
 //        thin panels and small grids)
 sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
+// closure_persistent.cu: the whole u8/u16 closure in one persistent launch (64-wide pivot
+// blocks, work items in a dependency order, bounded waits on per-block versions).
+constexpr int64_t kPersistentMaxD = 32768;
+// D from which the persistent schedule is the automatic choice; above kPersistentMaxD: never
+// (measured slower than the stream schedules at every size so far)
+constexpr int64_t kPersistentAutoMinU8 = kPersistentMaxD + 1, kPersistentAutoMinU16 = kPersistentMaxD + 1;
+size_t antidist_closure_persistent_workspace(int64_t D);   // 0: not available for this D
+sr_status launch_antidist_closure_persistent(void *T, int64_t ldt, int D, sr_dtype dt, void *ws, size_t ws_bytes,
+                                             int *status, int spin_limit, int frac, cudaStream_t s);
+// The work order as (type, pivot block, tile row, tile column, second tile column or -1)
+// 5-tuples: type 0 phase-3 tiles, 1 row-panel tile, 2 column-panel tile, 3 diagonal block.
+// Returns the item count (-1 outside the persistent schedule's range); writes min(cap,
+// count) items to out.
+long long antidist_closure_persistent_order(int64_t D, int frac, int *out, long long cap);
 // closure.cu; width: block width of the blocked closure (0 = automatic, 128, 256, 512)
 sr_status launch_antidist_closure(void *T, int64_t ldt, int D, sr_dtype dt, bool vec, cudaStream_t s,
                                   int width = 0);

@@ -22,6 +22,9 @@ assert L.bool_mul(None, 16, 1, 16, 1, 16, 1, 4, 4, 4, sr.SR_BOOL_W32, 0, None) =
 assert L.antidist_mul(None, 1, 4, 1, 4, 2, 4, 4, 4, 4, 0, 0, None) == sr.SR_EINVAL
 assert L.sr_cancel(None, 1) == sr.SR_EINVAL
 assert L.sr_serve_start(None, None) == sr.SR_EINVAL
+assert L.bool_closure_squaring_noalloc(None, 1, 4, sr.SR_U8, None) == sr.SR_EINVAL
+assert L.sr_batch_create(None, None, 0, None) == sr.SR_EINVAL
+assert L.sr_batched(None, None, 0, None) == sr.SR_EINVAL
 rec = ctypes.CDLL(sys.argv[1])
 rec.nvtx_record_log.restype = ctypes.c_char_p
 sys.stdout.write(rec.nvtx_record_log().decode())
@@ -47,7 +50,9 @@ def test_entry_points_open_and_close_ranges(recorder):
     assert r.returncode == 0, r.stderr
     lines = [l.split(" ", 2) for l in r.stdout.strip().splitlines()]
     pushes = [l[2] for l in lines if l[0] == "push"]
-    assert pushes == ["antidist_closure", "bool_mul", "antidist_mul", "sr_cancel", "sr_serve_start"]
+    assert pushes == ["antidist_closure", "bool_mul", "antidist_mul", "sr_cancel", "sr_serve_start",
+                      "bool_closure_squaring_noalloc", "sr_batch_create", "sr_batched", "sr_batch_create"]
     assert all(l[1] == "semiring" for l in lines)
     # strictly nested: each push is closed by the next pop, even on the error paths
-    assert [l[0] for l in lines] == ["push", "pop"] * 5
+    # sr_batched opens its own range around the nested sr_batch_create
+    assert [l[0] for l in lines] == ["push", "pop"] * 7 + ["push", "push", "pop", "pop"]
