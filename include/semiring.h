@@ -125,11 +125,12 @@ typedef enum {
                                 products; their diagonal blocks are closed at width 128.
                                 A width other than 0 also turns the persistent schedule off. */
     SR_OPT_CLOSURE_PERSISTENT = 5, /* u8/u16 anti-distance closure in one persistent launch
-                                (64-wide pivot blocks; work items taken in a dependency order,
+                                (128-wide pivot blocks; work items taken in a dependency order,
                                 each waiting, bounded by SR_OPT_SPIN_LIMIT, on per-block
                                 counters): 0 never, 1 automatic (default; the stream schedule
-                                is faster at every size measured so far), 2 whenever possible.  Needs 16-byte aligned rows, 128 <= D <=
-                                32768 and a ctx workspace of sr_workspace_query(
+                                is faster at every size measured so far), 2 whenever
+                                possible.  Needs 16-byte aligned rows, 256 <= D <= 32768
+                                and a ctx workspace of sr_workspace_query(
                                 SR_OP_ANTIDIST_CLOSURE, dtype, D, 0, ..) bytes; without them the
                                 stream schedule runs. */
     SR_OPT_CLOSURE_PANEL_SHARE = 6 /* persistent closure: share of each pivot block's phase-3
@@ -145,7 +146,7 @@ sr_status sr_set_option(sr_ctx *ctx, int option, int value);
  * or -1) — type 0: 128x128 phase-3 tiles (i, j) and (i, j2) on the grid without block
  * row/column s (Section 2 Warshall step, T_ij ⊕= T_is ⊗ T_sj); 1: a row-panel tile j;
  * 2: a column-panel tile i; 3: the diagonal block s — and returns the item count, or -1
- * if D is outside [128, 32768]. */
+ * if D is outside [256, 32768]. */
 long long sr_closure_order(int64_t D, int share, int *out, long long cap);
 
 /* ---------------------------------------------------------------- encoding (Sections 3-4) */

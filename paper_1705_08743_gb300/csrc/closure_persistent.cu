@@ -1,7 +1,7 @@
 // The whole anti-distance closure (u8, u16) in one persistent launch.
 //
 // Method: Section 2's Warshall loop, generalised by Section 3 to anti-distance
-// matrices (Floyd), in the blocked three-phase order with 64-wide pivot blocks:
+// matrices (Floyd), in the blocked three-phase order with 128-wide pivot blocks:
 // for pivot block s, the diagonal block is closed (phase 1), the row and column
 // panels take T_sj := T_sj ⊕ T_ss ⊗ T_sj and T_is := T_is ⊕ T_is ⊗ T_ss
 // (phase 2), and every other block takes T_ij ⊕= T_is ⊗ T_sj (phase 3).
@@ -10,11 +10,11 @@
 // ramp-up and a partly empty last wave of CTAs.  Here every CTA pulls work items
 // from one counter, in a fixed order, until none are left: phase-3 tiles of
 // 128×128 entries (on the grid of the matrix without block row and column s),
-// panel tiles of 64×128 / 128×64 entries, and diagonal blocks.  The tail of one
+// panel tiles of the same size, and diagonal blocks.  The tail of one
 // pivot block's phase 3 overlaps the next one's, and the next diagonal block and
 // panels are computed beside the bulk of the current phase 3.
 //
-// Ordering.  Every 64×64 block (I, J) carries a version: the number of pivot
+// Ordering.  Every 128×128 block (I, J) carries a version: the number of pivot
 // blocks already applied to it.  Each pivot block s updates each block exactly
 // once (phase 3 if I ≠ s ≠ J, a panel if one of them is s, phase 1 if both), so
 // an item of pivot block s waits until the blocks it writes have version s and
@@ -44,7 +44,9 @@
 namespace sr {
 namespace {
 
-constexpr int PW = 64;          // pivot block width
+constexpr int PW = 128;         // pivot block width
+constexpr int BPT = 1;          // pivot blocks per phase-3 tile side (TT / PW)
+constexpr int PBK = 32;         // k-panel depth of the product tiles (deeper panels spill registers)
 constexpr int TT = 128;         // phase-3 tile (entries per side)
 constexpr int PC_COMPUTE = 128;    // four compute warps
 constexpr int PC_THREADS = 160;    // and one control warp
@@ -81,12 +83,12 @@ struct Item {
 __host__ __device__ __forceinline__ int t3_of(const PcArgs &a, int s) { return s == a.nb - 1 ? a.t3l : a.t3m; }
 __host__ __device__ __forceinline__ int skip_s(int x, int s) { return x < s ? x : x + 1; }   // grid block -> matrix block
 
-// Tile rows/columns of pivot step s's cross: c0 and c0 + 1 with c0 = min(s / 2, T - 2)
-// (one when T = 1).  They hold matrix blocks s + 1 .. s + 3 (grid indices s .. s + 2) where
-// the grid has them: block s + 1 feeds the next diagonal block and panels, blocks s + 2 and
-// s + 3 the next step's cross.
+// Tile rows/columns of pivot step s's cross: c0 and c0 + 1 with c0 = min(s / BPT, T - 2)
+// (one when T = 1).  They hold the matrix blocks after s (grid indices s, s + 1, ...) where
+// the grid has them: block s + 1 feeds the next diagonal block and panels, the blocks after
+// it the next step's cross.
 __host__ __device__ __forceinline__ int cross_count(int T) { return T >= 2 ? 2 : 1; }
-__host__ __device__ __forceinline__ int cross_first(int T, int s) { return T >= 2 ? imin(s / 2, T - 2) : 0; }
+__host__ __device__ __forceinline__ int cross_first(int T, int s) { return T >= 2 ? imin(s / BPT, T - 2) : 0; }
 
 // Items of pivot step s's sequence: the cross (single tiles), the next diagonal block,
 // (T - nc) rows of ceil((T - nc) / 2) two-tile items, the next pivot block's 2·Tn panel tiles.
@@ -100,7 +102,7 @@ __host__ __device__ __forceinline__ long long seq_len(int T, bool next, int Tn)
 // Panel items of pivot block p, m in [0, 2·T): the tiles that hold block p + 1 come first.
 __host__ __device__ __forceinline__ Item panel_item(const PcArgs &a, int p, int m)
 {
-    const int T = t3_of(a, p), c1 = imin(p / 2, T - 1);
+    const int T = t3_of(a, p), c1 = imin(p / BPT, T - 1);
     if (m < 2) return {m == 0 ? IT_ROW : IT_COL, p, c1, c1, -1};
     const int u = (m - 2) >> 1, t = u < c1 ? u : u + 1;
     return {((m - 2) & 1) ? IT_COL : IT_ROW, p, t, t, -1};
@@ -117,7 +119,7 @@ __host__ __device__ __forceinline__ Item step_item(const PcArgs &a, int s, long 
     const int P = (Tr + 1) / 2;                            // two-tile items per row outside the cross
     const long long X = (long long)T * T - (long long)Tr * Tr, R = (long long)Tr * P, F = R * a.frac / 256;
     if (r < X) {
-        const int d = imin(s / 2, T - 1);                  // the tile that holds block s + 1
+        const int d = imin(s / BPT, T - 1);                // the tile that holds block s + 1
         int m = (int)r;
         if (m == 0) return {IT_P3, s, d, d, -1};
         m -= 1;
@@ -191,7 +193,7 @@ __host__ __device__ __forceinline__ Blocks written(const PcArgs &a, const Item &
     const int nbc = a.nb - 1;      // blocks on the grid without block s
     b.nr = b.nc = 0;
     auto two = [&](int t, int *dst, int &n) {
-        for (int x = 2 * t; x < 2 * t + 2 && x < nbc; ++x) dst[n++] = skip_s(x, it.s);
+        for (int x = BPT * t; x < BPT * t + BPT && x < nbc; ++x) dst[n++] = skip_s(x, it.s);
     };
     if (it.type == IT_DIAG) {
         b.r[0] = b.c[0] = it.s;
@@ -245,59 +247,46 @@ __device__ __forceinline__ void publish_warp(const PcArgs &a, const Item &it, co
     if (lane < nw) st_release(a.ver + (int64_t)b.r[lane / b.nc] * a.nb + b.c[lane % b.nc], it.s + 1);
 }
 
-// ---------------------------------------------------------------- phase 1: one 64×64 block
-// Plain Warshall/Floyd over the block's bw pivots, in registers: thread t holds row
-// t / 2, entries [32·(t % 2), +32) as 16 lane pairs.  Before pivot k the two threads of
-// row k publish it in shared memory (double-buffered, one barrier per pivot); entry
-// (r, k) comes from the register of the thread holding column k, by a shuffle within
-// the pair of lanes.  Row k and column k do not change at pivot k (T_kk ⊗ x <= x).
-template <class KD>
-__device__ void close_diag(const PcArgs &a, int s)
+// ---------------------------------------------------------------- phase 1: one 128×128 block
+// The block sits in shared memory as 16-bit lane pairs (entry c of row r in the low or
+// high half of word r·LDX + c/2; rows padded to LDX words).  It is closed by the same
+// three phases once more on its two 64-wide halves: close X00; X01 ⊕= X00 ⊗ X01 and
+// X10 ⊕= X10 ⊗ X00; X11 ⊕= X10 ⊗ X01; close X11; X10 ⊕= X11 ⊗ X10 and X01 ⊕= X01 ⊗ X11;
+// X00 ⊕= X01 ⊗ X10.  Entries outside the block (a ragged last block) are 0, and 0 ⊗ x =
+// x ⊗ 0 = 0, so every step may run over the full 64 pivots.
+constexpr int LDX = 68;                     // words per staged row (16-byte aligned rows)
+constexpr size_t DIAG_SMEM = (size_t)(PW * LDX + 64) * sizeof(uint32_t);
+
+// thread (r, h) = (tid / 2, tid % 2) holds row r, lane pairs [16h, 16h + 16) of a 64-wide half
+__device__ __forceinline__ void load16(const uint32_t *src, uint32_t (&x)[16])
 {
-    using E = typename KD::elem;
-    E *T = static_cast<E *>(a.T);
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *piv = smem;                                   // [2][32] lane pairs
-    const int tid = threadIdx.x, r = tid >> 1, h = tid & 1;
-    const int k0 = s * PW, bw = min(PW, a.D - k0);
-    constexpr int CH = 16 / (int)sizeof(E);                 // entries per 16-byte chunk
-    constexpr int NCH = 32 / CH;                            // chunks per half row
-    const int c0 = 32 * h;
-    E *row = T + (int64_t)(k0 + r) * a.ldt + k0 + c0;
-    uint32_t x[16];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        const int col = c0 + c * CH;
-        if (r < bw && col < bw) {
-            if (col + CH <= bw) {
-                v = __ldcg(reinterpret_cast<const uint4 *>(row + c * CH));
-            } else {
-                uint32_t w[4] = {0u, 0u, 0u, 0u};
-                for (int t = 0; t < CH; ++t)
-                    if (col + t < bw)
-                        w[(t * sizeof(E)) / 4] |= (uint32_t)__ldcg(row + c * CH + t) << (8 * ((t * sizeof(E)) % 4));
-                v = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-        if (sizeof(E) == 1) {
-            x[8 * c + 0] = u8x2_lo(v.x); x[8 * c + 1] = u8x2_hi(v.x);
-            x[8 * c + 2] = u8x2_lo(v.y); x[8 * c + 3] = u8x2_hi(v.y);
-            x[8 * c + 4] = u8x2_lo(v.z); x[8 * c + 5] = u8x2_hi(v.z);
-            x[8 * c + 6] = u8x2_lo(v.w); x[8 * c + 7] = u8x2_hi(v.w);
-        } else {
-            x[4 * c + 0] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
-        }
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(src)[q];
+        x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
     }
+}
+__device__ __forceinline__ void store16(uint32_t *dst, const uint32_t (&x)[16])
+{
 #pragma unroll
-    for (int k = 0; k < PW; ++k) {
-        if (k >= bw) break;                                 // bw is the same for the whole CTA
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<uint4 *>(dst)[q] = make_uint4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+
+// Warshall/Floyd over the 64 pivots of the half-block at (o, o), o in {0, 64}: before pivot k
+// the two threads of row k publish it (double-buffered), one barrier per pivot; entry (r, k)
+// comes from the thread of row r that holds column k, by a shuffle within the lane pair.
+template <class KD>
+__device__ void close64(uint32_t *X, uint32_t *piv, int o)
+{
+    const int tid = threadIdx.x, r = tid >> 1, h = tid & 1;
+    uint32_t x[16];
+    uint32_t *row = X + (o + r) * LDX + o / 2 + 16 * h;
+    load16(row, x);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
         uint32_t *pb = piv + (k & 1) * 32;
-        if (r == k) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                reinterpret_cast<uint4 *>(pb + 16 * h)[q] = make_uint4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-        }
+        if (r == k) store16(pb + 16 * h, x);
         tile_sync<BAR_TILE>();
         const uint32_t mine = x[(k >> 1) & 15];
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
@@ -313,26 +302,103 @@ __device__ void close_diag(const PcArgs &a, int s)
             x[4 * q + 3] = KD::op(x[4 * q + 3], v.w, a0, a1);
         }
     }
-    if (r < bw) {
+    store16(row, x);
+}
+
+// C ⊕= A ⊗ B on 64-wide halves: C at (cr, cc), A at (ar, ac), B at (br, bc) (entry offsets).
+// A in-place update (C sharing rows with A or B) reads a mix of old and new entries, which
+// the monotone ⊗ makes harmless.
+template <class KD>
+__device__ void mul64(uint32_t *X, int cr, int cc, int ar, int ac, int br, int bc)
+{
+    const int tid = threadIdx.x, r = tid >> 1, h = tid & 1;
+    uint32_t x[16];
+    uint32_t *crow = X + (cr + r) * LDX + cc / 2 + 16 * h;
+    const uint32_t *arow = X + (ar + r) * LDX + ac / 2;
+    const uint32_t *b0 = X + br * LDX + bc / 2 + 16 * h;
+    load16(crow, x);
+#pragma unroll 4
+    for (int k = 0; k < 64; ++k) {
+        uint32_t a0, a1;
+        KD::bcast((arow[k >> 1] >> (16 * (k & 1))) & 0xFFFFu, a0, a1);
+        const uint4 *bv = reinterpret_cast<const uint4 *>(b0 + k * LDX);
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const int col = c0 + c * CH;
-            if (col >= bw) continue;
-            uint4 v;
-            if (sizeof(E) == 1)
-                v = make_uint4(pack_u8x4(x[8 * c], x[8 * c + 1]), pack_u8x4(x[8 * c + 2], x[8 * c + 3]),
-                               pack_u8x4(x[8 * c + 4], x[8 * c + 5]), pack_u8x4(x[8 * c + 6], x[8 * c + 7]));
-            else
-                v = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = bv[q];
+            x[4 * q] = KD::op(x[4 * q], v.x, a0, a1);
+            x[4 * q + 1] = KD::op(x[4 * q + 1], v.y, a0, a1);
+            x[4 * q + 2] = KD::op(x[4 * q + 2], v.z, a0, a1);
+            x[4 * q + 3] = KD::op(x[4 * q + 3], v.w, a0, a1);
+        }
+    }
+    store16(crow, x);
+}
+
+template <class KD>
+__device__ void close_diag(const PcArgs &a, int s)
+{
+    using E = typename KD::elem;
+    E *T = static_cast<E *>(a.T);
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *X = smem, *piv = smem + PW * LDX;
+    const int tid = threadIdx.x;
+    const int k0 = s * PW, bw = min(PW, a.D - k0);
+    constexpr int CH = 16 / (int)sizeof(E), CPR = PW / CH;       // entries per chunk, chunks per row
+    // stage: 16-byte chunks through L2, zero outside the block
+    for (int c = tid; c < PW * CPR; c += PC_COMPUTE) {
+        const int r = c / CPR, col = (c % CPR) * CH;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < bw && col < bw) {
+            const E *src = T + (int64_t)(k0 + r) * a.ldt + k0 + col;
             if (col + CH <= bw) {
-                *reinterpret_cast<uint4 *>(row + c * CH) = v;
+                v = __ldcg(reinterpret_cast<const uint4 *>(src));
             } else {
-                const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
                 for (int t = 0; t < CH; ++t)
-                    if (col + t < bw)
-                        row[c * CH + t] = (E)((w4[(t * sizeof(E)) / 4] >> (8 * ((t * sizeof(E)) % 4))) &
-                                              (sizeof(E) == 1 ? 0xFFu : 0xFFFFu));
+                    if (col + t < bw) w[(t * sizeof(E)) / 4] |= (uint32_t)__ldcg(src + t) << (8 * ((t * sizeof(E)) % 4));
+                v = make_uint4(w[0], w[1], w[2], w[3]);
             }
+        }
+        uint32_t *d = X + r * LDX + col / 2;
+        if (sizeof(E) == 1) {
+            reinterpret_cast<uint4 *>(d)[0] = make_uint4(u8x2_lo(v.x), u8x2_hi(v.x), u8x2_lo(v.y), u8x2_hi(v.y));
+            reinterpret_cast<uint4 *>(d)[1] = make_uint4(u8x2_lo(v.z), u8x2_hi(v.z), u8x2_lo(v.w), u8x2_hi(v.w));
+        } else {
+            reinterpret_cast<uint4 *>(d)[0] = v;
+        }
+    }
+    tile_sync<BAR_TILE>();
+    close64<KD>(X, piv, 0);
+    tile_sync<BAR_TILE>();
+    mul64<KD>(X, 0, 64, 0, 0, 0, 64);                      // X01 ⊕= X00 ⊗ X01
+    mul64<KD>(X, 64, 0, 64, 0, 0, 0);                      // X10 ⊕= X10 ⊗ X00
+    tile_sync<BAR_TILE>();
+    mul64<KD>(X, 64, 64, 64, 0, 0, 64);                    // X11 ⊕= X10 ⊗ X01
+    tile_sync<BAR_TILE>();
+    close64<KD>(X, piv, 64);
+    tile_sync<BAR_TILE>();
+    mul64<KD>(X, 64, 0, 64, 64, 64, 0);                    // X10 ⊕= X11 ⊗ X10
+    mul64<KD>(X, 0, 64, 0, 64, 64, 64);                    // X01 ⊕= X01 ⊗ X11
+    tile_sync<BAR_TILE>();
+    mul64<KD>(X, 0, 0, 0, 64, 64, 0);                      // X00 ⊕= X01 ⊗ X10
+    tile_sync<BAR_TILE>();
+    for (int c = tid; c < PW * CPR; c += PC_COMPUTE) {
+        const int r = c / CPR, col = (c % CPR) * CH;
+        if (r >= bw || col >= bw) continue;
+        const uint32_t *q = X + r * LDX + col / 2;
+        E *dst = T + (int64_t)(k0 + r) * a.ldt + k0 + col;
+        uint4 v;
+        if (sizeof(E) == 1)
+            v = make_uint4(pack_u8x4(q[0], q[1]), pack_u8x4(q[2], q[3]), pack_u8x4(q[4], q[5]), pack_u8x4(q[6], q[7]));
+        else
+            v = make_uint4(q[0], q[1], q[2], q[3]);
+        if (col + CH <= bw) {
+            *reinterpret_cast<uint4 *>(dst) = v;
+        } else {
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+            for (int t = 0; t < CH; ++t)
+                if (col + t < bw)
+                    dst[t] = (E)((w4[(t * sizeof(E)) / 4] >> (8 * ((t * sizeof(E)) % 4))) & (sizeof(E) == 1 ? 0xFFu : 0xFFFFu));
         }
     }
 }
@@ -356,29 +422,31 @@ __device__ __forceinline__ void run_product(const PcArgs &a, const Item &it)
         p.rskip0 = k0; p.rskipw = bw; p.cskip0 = k0; p.cskipw = bw;
         const int t1 = it.i * tn + it.j;
         if (it.j2 < 0)
-            mul_tiles<KD, TT, TT, 32, 8, 16, true, true, BAR_TILE>(p, t1, tn * tn, t1 + 1);
+            mul_tiles<KD, TT, TT, PBK, 8, 16, true, true, BAR_TILE>(p, t1, tn * tn, t1 + 1);
         else                          // two tiles of row i; the second's first k-panel loads during the first
-            mul_tiles<KD, TT, TT, 32, 8, 16, true, true, BAR_TILE>(p, t1, it.j2 - it.j, it.i * tn + it.j2 + 1);
+            mul_tiles<KD, TT, TT, PBK, 8, 16, true, true, BAR_TILE>(p, t1, it.j2 - it.j, it.i * tn + it.j2 + 1);
     } else if (it.type == IT_ROW) {  // T_sj := T_sj ⊕ T_ss ⊗ T_sj, in place
         p.A = T + (int64_t)k0 * ld + k0; p.B = T + (int64_t)k0 * ld; p.C = T + (int64_t)k0 * ld;
         p.R = bw; p.N = Dc;
         p.rskip0 = 0x7fffffff; p.rskipw = 0; p.cskip0 = k0; p.cskipw = bw;
-        mul_tiles<KD, PW, TT, 32, 4, 16, true, true, BAR_TILE>(p, it.j, tn);
+        mul_tiles<KD, PW, TT, PBK, PW / 16, 16, true, true, BAR_TILE>(p, it.j, tn);
     } else {                          // T_is := T_is ⊕ T_is ⊗ T_ss, in place
         p.A = T + k0; p.B = T + (int64_t)k0 * ld + k0; p.C = T + k0;
         p.R = Dc; p.N = bw;
         p.rskip0 = k0; p.rskipw = bw; p.cskip0 = 0x7fffffff; p.cskipw = 0;
-        mul_tiles<KD, TT, PW, 32, 8, 8, true, true, BAR_TILE>(p, it.i, tn);
+        mul_tiles<KD, TT, PW, PBK, 8, PW / 8, true, true, BAR_TILE>(p, it.i, tn);
     }
 }
 
 template <class KD>
 struct PcCfg {
-    using P3 = MulCfg<KD, TT, TT, 32, 8, 16>;
-    static constexpr size_t SMEM = std::max({P3::SMEM, MulCfg<KD, PW, TT, 32, 4, 16>::SMEM,
-                                             MulCfg<KD, TT, PW, 32, 8, 8>::SMEM, (size_t)256});
-    static_assert(P3::THREADS == PC_COMPUTE && MulCfg<KD, PW, TT, 32, 4, 16>::THREADS == PC_COMPUTE &&
-                  MulCfg<KD, TT, PW, 32, 8, 8>::THREADS == PC_COMPUTE, "one compute shape for every item");
+    using P3 = MulCfg<KD, TT, TT, PBK, 8, 16>;
+    using Row = MulCfg<KD, PW, TT, PBK, PW / 16, 16>;
+    using Col = MulCfg<KD, TT, PW, PBK, 8, PW / 8>;
+    static constexpr size_t SMEM = std::max({P3::SMEM, Row::SMEM, Col::SMEM, DIAG_SMEM});
+    static_assert(P3::THREADS == PC_COMPUTE && Row::THREADS == PC_COMPUTE && Col::THREADS == PC_COMPUTE,
+                  "one compute shape for every item");
+    static_assert(BPT * PW == TT, "phase-3 tiles hold whole pivot blocks");
     // CTAs per SM the register budget is sized for: u8 two (three would cap a thread at
     // 128 registers and spill the product tile's accumulators), u16 one (its 115 KB of
     // shared memory fit once)

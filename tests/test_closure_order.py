@@ -21,18 +21,19 @@ import pytest
 import oracle
 import synth
 
-PW, TT = 64, 128
+PW, TT = 128, 128          # pivot block width, phase-3 tile side
+BPT = TT // PW
 
 
 def _blocks(item, nb):
     """(written blocks, operand blocks and the version each needs) of an item, from
-    the definitions: tile (i, j) of pivot block s lies on the grid of 64-blocks without
-    block row and column s, two grid blocks per tile side."""
+    the definitions: tile (i, j) of pivot block s lies on the grid of pivot-width blocks
+    without block row and column s, BPT grid blocks per tile side."""
     typ, s, i, j, j2 = item
     nbc = nb - 1
 
     def two(t):
-        return [x if x < s else x + 1 for x in (2 * t, 2 * t + 1) if x < nbc]
+        return [x if x < s else x + 1 for x in range(BPT * t, BPT * t + BPT) if x < nbc]
 
     if typ == 3:
         return [(s, s)], []
@@ -44,7 +45,7 @@ def _blocks(item, nb):
     return [(r, s) for r in two(i)], [(s, s)]
 
 
-@pytest.mark.parametrize("D", [128, 129, 191, 192, 200, 257, 320, 1000, 1024, 1500, 2085, 4096])
+@pytest.mark.parametrize("D", [256, 257, 383, 384, 400, 513, 640, 1000, 1024, 1500, 2085, 4096, 8192])
 @pytest.mark.parametrize("share", [0, 128, 256])
 def test_order_respects_dependencies_and_covers_every_block(D, share):
     from paper_1705_08743_gb300 import _capi as sr
@@ -74,7 +75,8 @@ def test_order_respects_dependencies_and_covers_every_block(D, share):
 
 def test_order_rejects_sizes_outside_its_range():
     from paper_1705_08743_gb300 import _capi as sr
-    assert sr.lib.sr_closure_order(127, 128, None, 0) == -1
+    assert sr.lib.sr_closure_order(255, 128, None, 0) == -1
+    assert sr.lib.sr_closure_order(256, 128, None, 0) > 0
     assert sr.lib.sr_closure_order(32769, 128, None, 0) == -1
     assert sr.lib.sr_closure_order(32768, 128, None, 0) > 0
 
@@ -111,7 +113,7 @@ def _run_item(T, item, D, S):
         T[rows, ks] = np.maximum(T[rows, ks], _mul(T[rows, ks], T[ks, ks], S))
 
 
-@pytest.mark.parametrize("D,seed", [(200, 0), (301, 1), (390, 2)])
+@pytest.mark.parametrize("D,seed", [(300, 0), (401, 1), (520, 2)])
 def test_items_in_random_dependency_orders_give_the_closure(D, seed):
     """Execute the items with numpy, each time picking at random one of the next few
     items of the order whose dependencies are met (as concurrent CTAs might finish
