@@ -404,10 +404,27 @@ static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s)
     return SR_OK;
 }
 
-sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles)
+// Tile rows per group of the tile order for a deep product: enough that a wave of CTAs
+// reuses A's row panels from L2, few enough that the group's panels of A (g · 128 rows · K)
+// stay within about 32 MB of L2 beside the column panels of B streaming through.  Shallow
+// products (the closure's K = 128..512 passes) keep the row-major order: their operands
+// are small and stay in L2 anyway.
+int group_rows(int R, int K, int esize, int bm)
 {
-    if (a.R <= 0 || a.N <= 0)
+    if (K < 1024) return 0;
+    const int64_t per_row = (int64_t)bm * K * esize;
+    const int tiles_m = (R + bm - 1) / bm;
+    const int g = (int)std::max<int64_t>(1, ((int64_t)32 << 20) / per_row);
+    return g >= tiles_m ? 0 : g;
+}
+
+sr_status launch_antidist_mul(const MulArgs &a0, sr_dtype dt, bool vec, cudaStream_t s, int tiles)
+{
+    if (a0.R <= 0 || a0.N <= 0)
         return SR_OK;
+    MulArgs a = a0;
+    if (a.group_m == 0 && a.skip_tile < 0)
+        a.group_m = group_rows(a.R, a.K, dt == SR_U8 ? 1 : dt == SR_U16 ? 2 : 4, tiles == 1 ? 64 : 128);
     if (dt == SR_U32)
         return launch_antidist32_mul(a, vec, s, tiles);
     if (tiles == 1)

@@ -80,8 +80,14 @@ antidist32_mul_kernel(MulArgs p)
     static_assert(128 % BM == 0 && 128 % BN == 0, "tiles nest in the 128x128 grid of skip_tile");
     const int tile = blockIdx.x;
     const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-    const int tiles_n = (p.N + BN - 1) / BN;
-    const int row0 = (tile / tiles_n) * BM, col0 = (tile % tiles_n) * BN;
+    const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.R + BM - 1) / BM;
+    int trow = tile / tiles_n, tcol = tile % tiles_n;
+    if (p.group_m > 0) {             // column-major inside groups of group_m tile rows (A's panels reused from L2)
+        const int per = p.group_m * tiles_n, g0 = (tile / per) * p.group_m, gm = min(p.group_m, tiles_m - g0);
+        trow = g0 + (tile % per) % gm;
+        tcol = (tile % per) / gm;
+    }
+    const int row0 = trow * BM, col0 = tcol * BN;
     if (p.skip_tile >= 0) {          // skip_tile indexes the 128x128 tile grid
         const int tn128 = (p.N + 127) / 128;
         if (row0 / 128 == p.skip_tile / tn128 && col0 / 128 == p.skip_tile % tn128)

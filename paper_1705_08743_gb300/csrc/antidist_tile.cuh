@@ -109,7 +109,22 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
 
     const int tid = threadIdx.x;
     const int tc = tid % TC, tr = tid / TC;
-    const int tiles_n = (p.N + BN - 1) / BN, tiles = min(tiles_n * ((p.R + BM - 1) / BM), tile_end);
+    const int tiles_m = (p.R + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
+    const int tiles = min(tiles_n * tiles_m, tile_end);
+    // tile t -> (tile row, tile column): row-major, or column-major inside groups of group_m
+    // tile rows (a wave of CTAs then shares group_m row panels of A and a run of B's column
+    // panels in L2, where row-major order streams all of B through L2 once per wave)
+    auto tile_rc = [&](int t, int &trow, int &tcol) {
+        if (p.group_m <= 0) {
+            trow = t / tiles_n;
+            tcol = t % tiles_n;
+            return;
+        }
+        const int per = p.group_m * tiles_n, g0 = (t / per) * p.group_m, gm = min(p.group_m, tiles_m - g0);
+        const int w = t % per;
+        trow = g0 + w % gm;
+        tcol = w / gm;
+    };
     const int nkt = (p.K + BK - 1) / BK;
 
     // tiles tile0, tile0 + stride, ... of the row-major tile grid (one per CTA when stride >= tiles)
@@ -117,8 +132,10 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
     static_assert(128 % BM == 0 && 128 % BN == 0, "tiles nest in the 128x128 grid of skip_tile");
     const int tn128 = (p.N + 127) / 128;
     auto skipped = [&](int t) {
-        return p.skip_tile >= 0 && ((t / tiles_n) * BM) / 128 == p.skip_tile / tn128 &&
-               ((t % tiles_n) * BN) / 128 == p.skip_tile % tn128;
+        if (p.skip_tile < 0) return false;
+        int trow, tcol;
+        tile_rc(t, trow, tcol);
+        return (trow * BM) / 128 == p.skip_tile / tn128 && (tcol * BN) / 128 == p.skip_tile % tn128;
     };
     auto advance = [&](int t) {
         t += stride;
@@ -213,15 +230,20 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
     };
 
     if (tile < tiles) {
-        const int row0 = (tile / tiles_n) * BM, col0 = (tile % tiles_n) * BN;
+        int trow, tcol;
+        tile_rc(tile, trow, tcol);
+        const int row0 = trow * BM, col0 = tcol * BN;
         if (p.accumulate) cprefetch(row0, col0);
         gload(row0, col0, 0);
     }
 
     for (; tile < tiles; tile = advance(tile)) {
-        const int row0 = (tile / tiles_n) * BM, col0 = (tile % tiles_n) * BN;
+        int trow, tcol, ntr = 0, ntc = 0;
+        tile_rc(tile, trow, tcol);
+        const int row0 = trow * BM, col0 = tcol * BN;
         const int next = advance(tile);
-        const int nrow0 = (next / tiles_n) * BM, ncol0 = (next % tiles_n) * BN;
+        if (next < tiles) tile_rc(next, ntr, ntc);
+        const int nrow0 = ntr * BM, ncol0 = ntc * BN;
 
         // C joins the result only in the epilogue (⊕ = max is commutative), so its load,
         // issued before the k-loop, is hidden behind the k-loop

@@ -46,11 +46,13 @@ struct MulArgs {
     int rskip0, rskipw;
     int cskip0, cskipw;
     int skip_tile = -1;        // a tile (row-major index, 128x128 tiles) left untouched, or -1
+    int group_m = 0;           // tile order: 0 row-major; g > 0 column-major within groups of g tile rows
 };
 
 // tiles: 0 = 128x128 CTA tiles (throughput; u32: 128x64), 1 = 64x64 (latency: more CTAs for
 //        thin panels and small grids)
 sr_status launch_antidist_mul(const MulArgs &a, sr_dtype dt, bool vec, cudaStream_t s, int tiles = 0);
+int group_rows(int R, int K, int esize, int bm);   // tile rows per group of a deep product's tile order
 // closure_persistent.cu: the whole u8/u16 closure in one persistent launch (64-wide pivot
 // blocks, work items in a dependency order, bounded waits on per-block versions).
 constexpr int64_t kPersistentMaxD = 32768;
