@@ -253,6 +253,17 @@ sr_status sr_batch_get_tuning(const sr_batch *b, int *cluster, int *coop_thresho
  * best_ms (may be NULL) receives the best time per launch, or -1 if reused. */
 sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, double *best_ms);
 sr_status sr_batch_info(const sr_batch *b, int *ngraphs, int *nitems, double *ops);
+/* Per-graph completion times.  enable != 0: every later launch writes the device clock
+ * (ns) at its start and when each graph is complete — at the end of the graph's own
+ * closure in the persistent kernel, at the end of the last pivot step the graph takes
+ * part in for the grouped schedule (one more one-thread kernel per step) — into a
+ * device array the batch allocates now (8·(1 + n + steps) bytes); 0 frees it.  Either
+ * change discards a captured graph, which the next use_graph launch captures again. */
+sr_status sr_batch_set_timing(sr_batch *b, int enable);
+/* After a timed launch has completed (the caller synchronises its stream): ms[g] =
+ * time from the launch's start to graph g's completion, in the order of the batch's
+ * descriptors.  Copies the stamps with cudaMemcpy.  SR_EINVAL if timing is off. */
+sr_status sr_batch_completion_ms(const sr_batch *b, double *ms);
 void sr_batch_destroy(sr_batch *b);
 /* One-shot form: plan (using ctx's recorded tuning for this signature, if any),
  * launch, synchronise `stream`, free the plan. */

@@ -112,6 +112,8 @@ _SIGS = {
     "sr_batch_get_tuning": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "sr_batch_autotune": (_st, [_vp, _vp, _vp, _int, ctypes.POINTER(ctypes.c_double)]),
     "sr_batch_info": (_st, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
+    "sr_batch_set_timing": (_st, [_vp, _int]),
+    "sr_batch_completion_ms": (_st, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "sr_batch_destroy": (None, [_vp]),
     "sr_batched": (_st, [_vp, ctypes.POINTER(sr_desc), _int, _vp]),
     "dist_mul": (_st, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp]),
@@ -306,6 +308,18 @@ def sr_batch_info(batch):
     n, it, ops = _int(), _int(), ctypes.c_double()
     _check(lib.sr_batch_info(batch, ctypes.byref(n), ctypes.byref(it), ctypes.byref(ops)), "sr_batch_info")
     return n.value, it.value, ops.value
+
+
+def sr_batch_set_timing(batch, enable: bool = True):
+    _check(lib.sr_batch_set_timing(batch, 1 if enable else 0), "sr_batch_set_timing")
+
+
+def sr_batch_completion_ms(batch):
+    """Per-graph completion times (ms since the last timed launch's start), descriptor order."""
+    n, _, _ = sr_batch_info(batch)
+    out = (ctypes.c_double * n)()
+    _check(lib.sr_batch_completion_ms(batch, out), "sr_batch_completion_ms")
+    return list(out)
 
 
 def sr_batch_destroy(batch):

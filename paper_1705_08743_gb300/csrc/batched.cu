@@ -338,9 +338,21 @@ __device__ void close_graph(const BatchGraph &gr, int rank, int nc, uint32_t *sm
     }
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread writes the device clock (ns): the start of a batch launch, or the end of the
+// launches before it in the stream.
+__global__ void batch_stamp_kernel(uint64_t *at) { *at = global_ns(); }
+
+// done (may be null): done[g] = the device clock when graph g's closure is complete
 template <class KD, int PB, int NC>
 __global__ void __launch_bounds__(128) batched_closure_kernel(const BatchGraph *graphs, const BatchItem *items,
-                                                              int nitems, int *counter)
+                                                              int nitems, int *counter, uint64_t *done)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int item_idx;
@@ -363,9 +375,12 @@ __global__ void __launch_bounds__(128) batched_closure_kernel(const BatchGraph *
         const BatchItem item = items[it];
         if (item.coop) {
             close_graph<KD, PB, NC>(graphs[item.g[0]], rank, NC, smem);
+            if (done && rank == 0 && threadIdx.x == 0) done[item.g[0]] = global_ns();
         } else {
-            if (rank < item.n)
+            if (rank < item.n) {
                 close_graph<KD, PB, 1>(graphs[item.g[rank]], 0, 1, smem);
+                if (done && threadIdx.x == 0) done[item.g[rank]] = global_ns();
+            }
             if (NC > 1) cg::this_cluster().sync();
         }
     }
@@ -394,6 +409,9 @@ struct BatchPlan {
     MulArgs *d_gargs = nullptr;      // products, concatenated per step and kind
     int *d_gstart = nullptr;         // first tile of each product within its launch
     bool gvec = true;                // every graph 16-byte aligned
+    // completion stamps (sr_batch_set_timing): [0] launch start, [1 + g] graph g done
+    // (persistent kernel), [1 + n + kb] end of pivot step kb (grouped schedule); device clock ns
+    uint64_t *d_stamps = nullptr;
     // captured launch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -465,8 +483,9 @@ static sr_status launch_batched_nc(BatchPlan &p, cudaStream_t s)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = NC > 1 ? 1 : 0;
+    uint64_t *done = p.d_stamps ? p.d_stamps + 1 : nullptr;
     SR_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, (const BatchGraph *)p.d_graphs, (const BatchItem *)p.d_items,
-                                     p.nitems, p.d_counter));
+                                     p.nitems, p.d_counter, done));
     count_launches();
     return SR_OK;
 }
@@ -574,12 +593,22 @@ static sr_status enqueue_grouped(BatchPlan &p, cudaStream_t s)
                                            p.dtype, p.gvec, true, s));
         SR_TRY(launch_antidist_mul_grouped(p.d_gargs + st.p3_off, p.d_gstart + st.p3_off, st.np3, st.p3_tiles,
                                            p.dtype, p.gvec, false, s));
+        if (p.d_stamps) {                                  // graphs with kb + 1 blocks are done now
+            batch_stamp_kernel<<<1, 1, 0, s>>>(p.d_stamps + 1 + p.n + kb);
+            SR_CUDA_CHECK(cudaGetLastError());
+            count_launches();
+        }
     }
     return SR_OK;
 }
 
 static sr_status enqueue_batch(BatchPlan &p, cudaStream_t s)
 {
+    if (p.d_stamps) {
+        batch_stamp_kernel<<<1, 1, 0, s>>>(p.d_stamps);
+        SR_CUDA_CHECK(cudaGetLastError());
+        count_launches();
+    }
     if (p.nc == 0)
         return enqueue_grouped(p, s);
     SR_CUDA_CHECK(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
@@ -735,6 +764,47 @@ sr_status sr_batch_launch(sr_batch *b, int use_graph, void *stream)
     return SR_OK;
 }
 
+sr_status sr_batch_set_timing(sr_batch *b, int enable)
+{
+    SR_TRACE("sr_batch_set_timing");
+    if (!b)
+        return fail(SR_EINVAL, "sr_batch_set_timing: NULL batch");
+    BatchPlan &p = b->plan;
+    if ((enable != 0) == (p.d_stamps != nullptr))
+        return SR_OK;
+    if (p.exec) { cudaGraphExecDestroy(p.exec); p.exec = nullptr; }    // recaptured with or without stamps
+    if (p.graph) { cudaGraphDestroy(p.graph); p.graph = nullptr; }
+    if (!enable) {
+        cudaFree(p.d_stamps);
+        p.d_stamps = nullptr;
+        return SR_OK;
+    }
+    int maxnb = 0;
+    for (const auto &g : p.h_graphs) maxnb = std::max(maxnb, (g.D + 127) / 128);
+    SR_CUDA_CHECK(cudaMalloc(&p.d_stamps, sizeof(uint64_t) * (size_t)(1 + p.n + maxnb)));
+    SR_CUDA_CHECK(cudaMemset(p.d_stamps, 0, sizeof(uint64_t) * (size_t)(1 + p.n + maxnb)));
+    return SR_OK;
+}
+
+sr_status sr_batch_completion_ms(const sr_batch *b, double *ms)
+{
+    SR_TRACE("sr_batch_completion_ms");
+    if (!b || !ms)
+        return fail(SR_EINVAL, "sr_batch_completion_ms: NULL batch or output");
+    const BatchPlan &p = b->plan;
+    if (!p.d_stamps)
+        return fail(SR_EINVAL, "sr_batch_completion_ms: timing is off (sr_batch_set_timing)");
+    int maxnb = 0;
+    for (const auto &g : p.h_graphs) maxnb = std::max(maxnb, (g.D + 127) / 128);
+    std::vector<uint64_t> h((size_t)(1 + p.n + maxnb));
+    SR_CUDA_CHECK(cudaMemcpy(h.data(), p.d_stamps, sizeof(uint64_t) * h.size(), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < p.n; ++g) {
+        const uint64_t end = p.nc == 0 ? h[1 + p.n + (p.h_graphs[g].D + 127) / 128 - 1] : h[1 + g];
+        ms[g] = end >= h[0] ? (double)(end - h[0]) * 1e-6 : -1.0;
+    }
+    return SR_OK;
+}
+
 sr_status sr_batch_info(const sr_batch *b, int *ngraphs, int *nitems, double *ops)
 {
     SR_TRACE("sr_batch_info");
@@ -758,6 +828,7 @@ void sr_batch_destroy(sr_batch *b)
     if (p.d_items) cudaFree(p.d_items);
     if (p.d_counter) cudaFree(p.d_counter);
     if (p.d_gactive) cudaFree(p.d_gactive);
+    if (p.d_stamps) cudaFree(p.d_stamps);
     if (p.d_gargs) cudaFree(p.d_gargs);
     if (p.d_gstart) cudaFree(p.d_gstart);
     delete b;

@@ -89,6 +89,52 @@ def test_batched_grouped_schedule_in_cuda_graph():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("tuning", [(2, 256, 2), (0, 1, 1)])
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batched_completion_times(tuning, use_graph):
+    """Per-graph completion stamps (sr_batch_set_timing): every graph gets a time within
+    the launch, the grouped schedule's graphs finish no earlier than the graphs with
+    fewer pivot steps, the persistent kernel's graphs no later than the whole launch,
+    and the results are unchanged."""
+    import torch
+    from paper_1705_08743_gb300 import _capi as sr
+    sizes = [5, 64, 129, 300, 700, 1000, 33, 257]
+    mats = make_batch(sizes, np.uint16, seed=17)
+    devs = [to_dev(M) for M in mats]
+    descs = [sr.closure_desc(T, T.shape[1], M.shape[0], sr.SR_U16) for T, M in zip(devs, mats)]
+    b = sr.sr_batch_create(None, descs)
+    try:
+        sr.sr_batch_set_tuning(b, *tuning)
+        with pytest.raises(sr.SemiringError):
+            sr.sr_batch_completion_ms(b)                           # timing off
+        sr.sr_batch_set_timing(b, True)
+        s = torch.cuda.Stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            sr.sr_batch_launch(b, use_graph, s.cuda_stream)
+            e1.record(s)
+        torch.cuda.synchronize()
+        total = e0.elapsed_time(e1)
+        ms = sr.sr_batch_completion_ms(b)
+        assert len(ms) == len(sizes)
+        assert all(0.0 <= t <= total + 0.05 for t in ms), (ms, total)
+        if tuning[0] == 0:                                         # step ends are ordered by pivot steps
+            steps = [(D + 127) // 128 for D in sizes]
+            for i in range(len(sizes)):
+                for j in range(len(sizes)):
+                    if steps[i] < steps[j]:
+                        assert ms[i] <= ms[j]
+        sr.sr_batch_set_timing(b, False)
+        sr.sr_batch_launch(b, use_graph, s.cuda_stream)
+        torch.cuda.synchronize()
+    finally:
+        sr.sr_batch_destroy(b)
+    for M, T in zip(mats, devs):
+        assert np.array_equal(to_host(T, np.uint16), oracle.warshall(M, 65535))
+
+
+@pytest.mark.gpu
 def test_sr_batched_one_shot():
     from paper_1705_08743_gb300 import _capi as sr
     mats = make_batch([10, 90, 260], np.uint8, seed=5)
