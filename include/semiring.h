@@ -84,7 +84,10 @@ typedef struct sr_ctx sr_ctx;
 typedef struct {
     size_t workspace_bytes;    /* device workspace allocated by sr_create (0: none) */
     int spin_limit;            /* iterations before a device-side wait gives up (0: default) */
-    int reserved[6];
+    const char *tune_cache;    /* JSON file of autotuned choices (NULL: none); sr_create loads it
+                                  if it exists and was written on a GPU of the same name and SM
+                                  count, and each new tuning rewrites it (see sr_autotune_closure) */
+    int reserved[4];
 } sr_config;
 
 /* ---------------------------------------------------------------- context */
@@ -138,6 +141,45 @@ typedef enum {
                                 (0..256, default 128) */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
+
+/* ---------------------------------------------------------------- autotuner */
+
+/* Choices the autotuner records (sr_tune_get / sr_tune_set):
+ *   SR_OP_ANTIDIST_CLOSURE: 128, 256 or 512 (block width of the stream schedule) or
+ *                           SR_TUNE_PERSISTENT (the persistent schedule);
+ *   SR_OP_BOOL_MUL:         SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES (Four Russians) or
+ *                           SR_TUNE_BOOL_TENSOR;
+ *   SR_OP_ANTIDIST_MUL:     128 or 64 (CTA tile side).
+ * Choices are kept per (op, dtype, size bucket): buckets are 256, 384, 512, 768, 1024,
+ * ... (powers of two and 1.5 times them) and a size uses the smallest bucket >= it. */
+enum { SR_TUNE_BOOL_WORDS = 0, SR_TUNE_BOOL_TABLES = 1, SR_TUNE_BOOL_TENSOR = 2, SR_TUNE_PERSISTENT = 1 };
+
+/* Time every schedule of the anti-distance closure (dtype u8/u16/u32) on a scratch
+ * matrix of the bucket's order D' >= D (allocated and freed here; D' <= 65536) and record
+ * the fastest for the bucket: stream schedules with blocks of 128, 256 and 512, and the
+ * persistent schedule when the ctx workspace holds what it needs.  reps timed runs per
+ * candidate (best taken) after one untimed run, on `stream` (synchronised).  An existing
+ * choice is returned without timing unless force != 0.  antidist_closure and
+ * dist_closure then follow the choice while SR_OPT_CLOSURE_BLOCK is 0 and
+ * SR_OPT_CLOSURE_PERSISTENT is 1 (their defaults).  Rewrites the ctx's tune cache.
+ * Outputs (may be NULL): the choice and its time in ms. */
+sr_status sr_autotune_closure(sr_ctx *ctx, sr_dtype dtype, int64_t D, void *stream, int reps, int force,
+                              int *choice, double *best_ms);
+/* The same for the D×D×D product: op SR_OP_BOOL_MUL (Boolean dtype; masked-OR words,
+ * Four Russians tables, tensor cores when the ctx workspace allows) or
+ * SR_OP_ANTIDIST_MUL (u8/u16/u32; 128x128 or 64x64 tiles).  bool_mul / antidist_mul
+ * follow the choice for sizes of the bucket (max(R, K, N)) while SR_OPT_BOOL_TENSOR and
+ * SR_OPT_BOOL_FOUR_RUSSIANS are 1 (their defaults). */
+sr_status sr_autotune_mul(sr_ctx *ctx, int op, sr_dtype dtype, int64_t D, void *stream, int reps, int force,
+                          int *choice, double *best_ms);
+/* Read or set one recorded choice (SR_ENOTFOUND: none recorded); sr_tune_set rewrites the
+ * tune cache. */
+sr_status sr_tune_get(const sr_ctx *ctx, int op, sr_dtype dtype, int64_t D, int *choice, double *ms);
+sr_status sr_tune_set(sr_ctx *ctx, int op, sr_dtype dtype, int64_t D, int choice);
+/* Write every recorded choice (batches included) to a JSON file / merge one written by
+ * this library on a GPU of the same name and SM count (SR_EINVAL otherwise). */
+sr_status sr_tune_save(const sr_ctx *ctx, const char *path);
+sr_status sr_tune_load(sr_ctx *ctx, const char *path);
 
 /* The work order of the persistent anti-distance closure (SR_OPT_CLOSURE_PERSISTENT) for an
  * order-D matrix and panel share `share` (as SR_OPT_CLOSURE_PANEL_SHARE), for tests and

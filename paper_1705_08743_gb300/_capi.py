@@ -35,6 +35,7 @@ SR_OPT_SPIN_LIMIT = 3
 SR_OPT_CLOSURE_BLOCK = 4
 SR_OPT_CLOSURE_PERSISTENT = 5
 SR_OPT_CLOSURE_PANEL_SHARE = 6
+SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES, SR_TUNE_BOOL_TENSOR, SR_TUNE_PERSISTENT = 0, 1, 2, 1
 SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 
@@ -50,7 +51,7 @@ class SemiringError(RuntimeError):
 
 class sr_config(ctypes.Structure):
     _fields_ = [("workspace_bytes", ctypes.c_size_t), ("spin_limit", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("tune_cache", ctypes.c_char_p), ("reserved", ctypes.c_int * 4)]
 
 
 _vp, _i64, _int, _st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int
@@ -106,6 +107,14 @@ _SIGS = {
     "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
     "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
     "sr_closure_order": (ctypes.c_longlong, [_i64, _int, _vp, ctypes.c_longlong]),
+    "sr_autotune_closure": (_st, [_vp, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
+                                  ctypes.POINTER(ctypes.c_double)]),
+    "sr_autotune_mul": (_st, [_vp, _int, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "sr_tune_get": (_st, [_vp, _int, _int, _i64, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
+    "sr_tune_set": (_st, [_vp, _int, _int, _i64, _int]),
+    "sr_tune_save": (_st, [_vp, ctypes.c_char_p]),
+    "sr_tune_load": (_st, [_vp, ctypes.c_char_p]),
     "sr_batch_create": (_st, [_vp, ctypes.POINTER(sr_desc), _int, ctypes.POINTER(_vp)]),
     "sr_batch_launch": (_st, [_vp, _int, _vp]),
     "sr_batch_set_tuning": (_st, [_vp, _int, _int, _int]),
@@ -178,8 +187,9 @@ def version() -> str:
     return lib.sr_version().decode()
 
 
-def sr_create(workspace_bytes: int = 0, spin_limit: int = 0):
-    cfg = sr_config(workspace_bytes=workspace_bytes, spin_limit=spin_limit)
+def sr_create(workspace_bytes: int = 0, spin_limit: int = 0, tune_cache: str | None = None):
+    cfg = sr_config(workspace_bytes=workspace_bytes, spin_limit=spin_limit,
+                    tune_cache=tune_cache.encode() if tune_cache else None)
     h = _vp()
     _check(lib.sr_create(ctypes.byref(h), ctypes.byref(cfg)), "sr_create")
     return h.value
@@ -205,6 +215,43 @@ def sr_closure_order(D: int, share: int = 128):
     buf = (ctypes.c_int * (5 * n))()
     lib.sr_closure_order(D, share, ctypes.cast(buf, _vp), n)
     return [tuple(buf[5 * q:5 * q + 5]) for q in range(n)]
+
+
+def sr_autotune_closure(ctx, dtype: int, D: int, stream=None, reps: int = 2, force: bool = False):
+    """-> (choice, ms): block width 128/256/512 or SR_TUNE_PERSISTENT, and its time."""
+    ch, ms = _int(), ctypes.c_double()
+    _check(lib.sr_autotune_closure(ctx, dtype, D, _stream(stream), reps, 1 if force else 0, ctypes.byref(ch),
+                                   ctypes.byref(ms)), "sr_autotune_closure")
+    return ch.value, ms.value
+
+
+def sr_autotune_mul(ctx, op: int, dtype: int, D: int, stream=None, reps: int = 2, force: bool = False):
+    ch, ms = _int(), ctypes.c_double()
+    _check(lib.sr_autotune_mul(ctx, op, dtype, D, _stream(stream), reps, 1 if force else 0, ctypes.byref(ch),
+                               ctypes.byref(ms)), "sr_autotune_mul")
+    return ch.value, ms.value
+
+
+def sr_tune_get(ctx, op: int, dtype: int, D: int):
+    """-> (choice, ms), or None if nothing is recorded for that bucket."""
+    ch, ms = _int(), ctypes.c_double()
+    st = lib.sr_tune_get(ctx, op, dtype, D, ctypes.byref(ch), ctypes.byref(ms))
+    if st == SR_ENOTFOUND:
+        return None
+    _check(st, "sr_tune_get")
+    return ch.value, ms.value
+
+
+def sr_tune_set(ctx, op: int, dtype: int, D: int, choice: int):
+    _check(lib.sr_tune_set(ctx, op, dtype, D, choice), "sr_tune_set")
+
+
+def sr_tune_save(ctx, path: str):
+    _check(lib.sr_tune_save(ctx, path.encode()), "sr_tune_save")
+
+
+def sr_tune_load(ctx, path: str):
+    _check(lib.sr_tune_load(ctx, path.encode()), "sr_tune_load")
 
 
 def sr_stream_status(ctx, stream=None):

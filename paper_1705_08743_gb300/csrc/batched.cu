@@ -900,8 +900,10 @@ sr_status sr_batch_autotune(sr_ctx *ctx, sr_batch *b, void *stream, int reps, do
     cudaEventDestroy(e1);
     if (st != SR_OK)
         return st;
-    if (ctx)
+    if (ctx) {
         ctx->tune[sig] = {bc.nc, bc.thr, bc.cps};
+        SR_TRY(tune_persist(ctx));                              // the ctx's tune cache, if any
+    }
     if (best_ms) *best_ms = best;
     return sr_batch_set_tuning(b, bc.nc, bc.thr, bc.cps);
 }

@@ -163,6 +163,11 @@ sr_status sr_create(sr_ctx **out, const sr_config *cfg)
     if (cfg) {
         c->ws_bytes = cfg->workspace_bytes;
         c->spin_limit = cfg->spin_limit > 0 ? cfg->spin_limit : kDefaultSpinLimit;
+        const sr_status ts = tune_load_config(c, cfg->tune_cache);
+        if (ts != SR_OK) {
+            delete c;
+            return ts;
+        }
     }
     cudaError_t e = cudaMalloc(&c->d_status, sizeof(int) * 4);
     if (e != cudaSuccess) {
@@ -310,7 +315,7 @@ sr_status bool_unpack(sr_ctx *, const void *M, int64_t ldm, uint8_t *dense, int6
 }
 
 // ------------------------------------------------------------------ products
-sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
                        int64_t R, int64_t K, int64_t N, sr_dtype dtype, int accumulate, void *stream)
 {
     SR_TRACE("antidist_mul");
@@ -335,7 +340,9 @@ sr_status antidist_mul(sr_ctx *, const void *A, int64_t lda, const void *B, int6
     a.rskipw = a.cskipw = 0;
     a.skip_tile = -1;
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
-    return launch_antidist_mul(a, dtype, vec, S(stream));
+    int tile = 128;     // the autotuner's tile side for this size, if it recorded one
+    tune_lookup(ctx, tune_key("antidist_mul", dtype, std::max(R, std::max(K, N))), &tile);
+    return launch_antidist_mul(a, dtype, vec, S(stream), tile == 64 ? 1 : 0);
 }
 
 // tensor-core path when the context allows it and has the workspace
@@ -385,11 +392,21 @@ static sr_status bool_mul_impl(const void *A, int64_t lda, const void *B, int64_
     a.accumulate = accumulate ? 1 : 0;
     a.skip0 = 0x7fffffff; a.skipw = 0;
     a.skip0w = 0x7fffffff; a.skipww = 0;
+    const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
+    int tuned = 0;      // a recorded choice applies while both path options are automatic
+    if (ctx && ctx->bool_tc_mode == 1 && ctx->bool_m4r_mode == 1 &&
+        tune_lookup(ctx, tune_key("bool_mul", dtype, std::max(R, std::max(K, N))), &tuned)) {
+        if (tuned == SR_TUNE_BOOL_TENSOR && ws && bool_tc_workspace(R, K, N) <= ws_bytes && bool_tc_available())
+            return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, ctx->spin_limit, s);
+        if (tuned == SR_TUNE_BOOL_TABLES)
+            return launch_bool_mul_m4r(a, s);
+        if (tuned == SR_TUNE_BOOL_WORDS)
+            return launch_bool_mul(a, vec, s);
+    }
     if (use_tc(ctx, R, K, N, ws_bytes))
         return launch_bool_mul_tc(a, ws, ws_bytes, ctx->d_status, ctx->spin_limit, s);
     if (use_m4r(ctx, R, K, a.ncw))
         return launch_bool_mul_m4r(a, s);
-    const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
     return launch_bool_mul(a, vec, s);
 }
 
@@ -423,6 +440,16 @@ static int64_t persistent_min_d(sr_dtype t) { return t == SR_U8 ? kPersistentAut
 static sr_status closure_dispatch(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, bool vec,
                                   cudaStream_t s)
 {
+    int tuned = 0;      // a recorded choice applies while both options are automatic
+    if (c && c->closure_width == 0 && c->closure_persistent == 1 && tune_lookup(c, tune_key("closure", dtype, D), &tuned)) {
+        if (tuned != SR_TUNE_PERSISTENT)
+            return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, tuned);
+        const size_t need = antidist_closure_persistent_workspace(D);
+        if (vec && (dtype == SR_U8 || dtype == SR_U16) && need > 0 && c->ws && c->ws_bytes >= need)
+            return launch_antidist_closure_persistent(T, ldt, (int)D, dtype, c->ws, c->ws_bytes, c->d_status,
+                                                      c->spin_limit, c->closure_share, s);
+        return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, 0);
+    }
     if (c && vec && c->closure_width == 0 && c->closure_persistent > 0 && (dtype == SR_U8 || dtype == SR_U16) &&
         (c->closure_persistent == 2 || D >= persistent_min_d(dtype))) {
         const size_t need = antidist_closure_persistent_workspace(D);

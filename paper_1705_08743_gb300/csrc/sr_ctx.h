@@ -28,6 +28,9 @@ struct sr_ctx {
     int closure_share = 128;      // persistent closure: phase-3 share before the next panels (/256)
     sr::ServeState *serve = nullptr;
     std::map<std::string, std::array<int, 3>> tune;   // autotuned batch configurations by signature
+    // autotuned single-call choices by "op/dtype/D bucket": [choice, 0, 0, ms] (tune.cu)
+    std::map<std::string, std::array<double, 4>> tuned;
+    std::string tune_path;                            // JSON cache (sr_config.tune_cache), "" for none
 };
 
 namespace sr {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/semiring.h"
@@ -29,6 +30,12 @@ sr_status check_mat(const char *fn, const char *name, const void *p, int64_t ld,
                     sr_dtype t);
 // bool_tc.cu: fp8 tensor-pipe probe (tcgen05 kind::f8f6f4, 128x256x32 MMAs); flops = 2·M·N·K per MMA
 sr_status peak_tc_f8(int iters, cudaStream_t s, double *ms, double *mma_per_s, double *flops);
+// tune.cu: size buckets, keys and lookups of the autotuned choices, the cache file
+int64_t tune_bucket(int64_t D);
+std::string tune_key(const char *op, sr_dtype t, int64_t D);
+bool tune_lookup(const sr_ctx *c, const std::string &key, int *choice);
+sr_status tune_load_config(sr_ctx *c, const char *path);   // at sr_create; a missing file is fine
+sr_status tune_persist(const sr_ctx *c);                     // rewrite the cache, if the ctx has one
 constexpr int kSideStreams = 3;
 cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
