@@ -142,6 +142,17 @@ typedef enum {
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 
+/* ---------------------------------------------------------------- row-sharded products */
+
+/* Rows [*r0, *r1) of an R-row product for `rank` of `world` processes (one GPU each).
+ * The rows of P = A ⊗ B are independent (Section 2 product formula: row i of P needs
+ * row i of A and all of B), so a product shards by row blocks of A and C with B
+ * replicated and no reduction; each rank then calls antidist_mul / bool_mul on its
+ * rows.  Ranges are whole groups of `align` rows (the CTA tile height, 128, keeps every
+ * rank's tiles full), as even as possible, disjoint, in rank order, covering [0, R).
+ * Host only, no CUDA call. */
+sr_status sr_shard_rows(int64_t R, int world, int rank, int64_t align, int64_t *r0, int64_t *r1);
+
 /* ---------------------------------------------------------------- autotuner */
 
 /* Choices the autotuner records (sr_tune_get / sr_tune_set):

@@ -107,6 +107,7 @@ _SIGS = {
     "bool_closure": (_st, [_vp, _vp, _i64, _i64, _int, _int, _vp]),
     "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
     "sr_closure_order": (ctypes.c_longlong, [_i64, _int, _vp, ctypes.c_longlong]),
+    "sr_shard_rows": (_st, [_i64, _int, _int, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "sr_autotune_closure": (_st, [_vp, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
                                   ctypes.POINTER(ctypes.c_double)]),
     "sr_autotune_mul": (_st, [_vp, _int, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
@@ -252,6 +253,13 @@ def sr_tune_save(ctx, path: str):
 
 def sr_tune_load(ctx, path: str):
     _check(lib.sr_tune_load(ctx, path.encode()), "sr_tune_load")
+
+
+def sr_shard_rows(R: int, world: int, rank: int, align: int = 128):
+    """-> (r0, r1): this rank's rows of a row-sharded product."""
+    r0, r1 = _i64(), _i64()
+    _check(lib.sr_shard_rows(R, world, rank, align, ctypes.byref(r0), ctypes.byref(r1)), "sr_shard_rows")
+    return r0.value, r1.value
 
 
 def sr_stream_status(ctx, stream=None):

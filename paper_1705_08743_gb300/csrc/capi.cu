@@ -138,6 +138,18 @@ extern "C" {
 
 const char *sr_last_error(void) { return g_err.c_str(); }
 
+sr_status sr_shard_rows(int64_t R, int world, int rank, int64_t align, int64_t *r0, int64_t *r1)
+{
+    if (!r0 || !r1 || R < 0 || world < 1 || rank < 0 || rank >= world || align < 1)
+        return fail(SR_EINVAL, "sr_shard_rows: need R >= 0, 0 <= rank < world, align >= 1 and outputs");
+    // whole groups of `align` rows, as evenly as possible; the first R mod world groups get one more
+    const int64_t groups = (R + align - 1) / align, q = groups / world, rem = groups % world;
+    const int64_t g0 = rank * q + std::min<int64_t>(rank, rem), g1 = g0 + q + (rank < rem ? 1 : 0);
+    *r0 = std::min(R, g0 * align);
+    *r1 = std::min(R, g1 * align);
+    return SR_OK;
+}
+
 long long sr_closure_order(int64_t D, int share, int *out, long long cap)
 {
     return antidist_closure_persistent_order(D, share, out, cap);

@@ -407,3 +407,24 @@ def test_closures_from_two_host_threads():
         t.join(timeout=300)
     assert not any(t.is_alive() for t in th), "a worker did not finish"
     assert not errors, errors
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_sharded_product_blocks(world):
+    """The row-sharded product as each rank runs it (sr_shard_rows, then antidist_mul on
+    its rows of A and C with all of B): the row blocks, computed as separate products on
+    sub-matrix pointers, reassemble to the oracle's product (Section 2: rows of the
+    product are independent)."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    rng = np.random.default_rng(world)
+    R, K, N = 1000, 300, 700
+    A = rand_anti(rng, R, K, np.uint8, 0.3)
+    B = rand_anti(rng, K, N, np.uint8, 0.3)
+    Ad, Bd = to_dev(A), to_dev(B)
+    Cd = torch.zeros((R, N), dtype=torch.uint8, device="cuda")
+    for rank in range(world):
+        r0, r1 = sr.sr_shard_rows(R, world, rank, 128)
+        if r1 > r0:
+            sr.antidist_mul(None, Ad[r0:r1], K, Bd, N, Cd[r0:r1], N, r1 - r0, K, N, sr.SR_U8, 0)
+    assert np.array_equal(to_host(Cd, np.uint8), oracle.mul(A, B, 255))
