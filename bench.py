@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-8192", action="store_true", help="default workload: skip the D=8192 closure timing")
+    ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched (config 4) summary")
     ap.add_argument("--closure", default="auto", choices=["auto", "persistent", "stream"],
                     help="anti-distance closure schedule (auto: the library's choice with the workspace it asks for)")
     ap.add_argument("--tuning", default="", help="batched workloads: cluster,threshold,ctas_per_sm (skips autotune)")
@@ -1070,6 +1071,8 @@ def run_ours(args, world, rank, local):
     extra = {}
     if wl.D == 4096 and wl.dtype == "u8" and not args.no_8192:
         extra["closure_8192"] = closure_8192(dev, stream, flush, peak, local, args)
+    if wl.D == 4096 and wl.dtype == "u8" and not args.no_batched:
+        extra["batched_cfg4"] = batched_summary(dev, stream, flush, args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1139,6 +1142,51 @@ def closure_8192(dev, stream, flush, peak, local, args, reps=5):
     return {"workload": "antidist_closure D=8192 u8 (edge p=0.05, length U{1..31}, seed 1)", "reps": reps,
             "ms": avg, "ms_min": min(ms), "ms_max": max(ms), "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak, "clocks": clk}
+
+
+def batched_summary(dev, stream, flush, args, steps=5):
+    """Config 4 (2000 graphs, D log-uniform [32,1024], u16) beside the default step: the
+    autotuned batch launch timed `steps` times on restored inputs with the L2 flushed, its
+    fraction of the u16 pipe peak (probed now), each graph's completion time inside a
+    launch (device-clock stamps, every graph of `steps` launches), and a loop of single
+    calls on the same graphs."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    wl = Cfg4(2000)
+    pool, _ = wl.host_inputs()
+    wl.setup_device(pool, None, dev)
+    with torch.cuda.stream(stream):
+        pk = sr.sr_peak_probe(sr.SR_PEAK_U16_PAIR, iters=8192, blocks_per_sm=8, stream=stream.cuda_stream)[2] / 1e9
+        for _ in range(3):
+            wl.pre_step(stream)
+            wl.step(stream)
+    torch.cuda.synchronize()
+    ev = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            wl.pre_step(stream)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wl.step(stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    avg = sum(ms) / len(ms)
+    comp = wl.completion_ms(stream, flush, launches=steps)
+    loop_ms = wl.loop_of_single_calls_ms(stream, reps=1)
+    out = {"workload": wl.name, "tuning(cluster,coop_threshold,ctas_per_sm)": wl.tuning, "launches": steps,
+           "ms": avg, "value": wl.ops / (avg * 1e-3) / 1e9, "unit": UNIT, "peak": pk,
+           "frac": wl.ops / (avg * 1e-3) / 1e9 / pk,
+           "launch_ms": {"p50": pct(ms, 0.5), "p99": pct(ms, 0.99)},
+           "graph_completion_ms": {"p50": pct(comp, 0.5), "p99": pct(comp, 0.99), "samples": len(comp)},
+           "loop_of_single_calls_ms": loop_ms, "speedup_vs_loop": loop_ms / avg}
+    sr.sr_batch_destroy(wl.batch)
+    sr.sr_destroy(wl.ctx)
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 def cfg4_line(args, wl, world, value, ms_per_step, step_ms, pk_ops, cpu, e2e, launches, clk, stream, flush):
