@@ -312,41 +312,44 @@ bool_tc_persistent_kernel(const __grid_constant__ CUtensorMap tA, const __grid_c
                      : "memory");
 }
 
-// bits -> e4m3 bytes (1.0 = 0x38), rows x Kp, zero past K
-__global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp,
-                                   const int *run_if)
+// 32 bits -> 32 e4m3 bytes (1.0 = 0x38, 0 = 0x00), written as two 16-byte stores
+__device__ __forceinline__ void expand_word(uint32_t bits, uint8_t *dst)
 {
-    if (run_if && *run_if == 0) return;
+    uint32_t o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t nib = (bits >> (4 * q)) & 0xFu;
+        o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
+               ((nib & 8u) ? 0x38000000u : 0u);
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+// rows x Kp bytes of A, K-major: item t (one thread) expands word w of row r; zero past K
+__device__ __forceinline__ void expand_rows_items(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp,
+                                                  int64_t t0, int64_t stride)
+{
     const int64_t total = (int64_t)rows * (Kp / 32);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = t0; t < total; t += stride) {
         const int r = (int)(t / (Kp / 32)), w = (int)(t % (Kp / 32));
         const int lo = 32 * w;
         uint32_t bits = lo < K ? M[(int64_t)r * ldm + w] : 0u;
         if (lo + 32 > K) bits &= lo >= K ? 0u : (1u << (K - lo)) - 1u;
-        uint32_t o[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t nib = (bits >> (4 * q)) & 0xFu;
-            o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
-                   ((nib & 8u) ? 0x38000000u : 0u);
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (int64_t)r * Kp + lo);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        expand_word(bits, out + (int64_t)r * Kp + lo);
     }
 }
 
-// transpose + expand: out[n][k] = bit (k, n) of M (K rows of bits), rows n < N, zero past K
-__global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp,
-                                   const int *run_if)
+// transpose + expand: out[n][k] = bit (k, n) of M (K rows of bits), rows n < N, zero past K;
+// item t (one warp) transposes the 32 x 32 bits of word w of rows 32kb .. 32kb + 31
+__device__ __forceinline__ void expand_cols_items(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp,
+                                                  int64_t t0, int64_t stride)
 {
-    if (run_if && *run_if == 0) return;
     const int lane = threadIdx.x & 31;
     const int nwords = (N + 31) / 32, kblocks = Kp / 32;
     const int64_t total = (int64_t)nwords * kblocks;
-    const int64_t wid = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t t = wid; t < total; t += nw) {
+    for (int64_t t = t0; t < total; t += stride) {
         const int w = (int)(t / kblocks), kb = (int)(t % kblocks);
         const int k = 32 * kb + lane;
         const uint32_t word = k < K ? M[(int64_t)k * ldm + w] : 0u;   // row k, columns 32w .. 32w+31
@@ -357,18 +360,58 @@ __global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N,
             if (lane == j) mine = b;
         }
         const int n = 32 * w + lane;
-        if (n < N) {
-            uint32_t o[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t nib = (mine >> (4 * q)) & 0xFu;
-                o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
-                       ((nib & 8u) ? 0x38000000u : 0u);
-            }
-            uint4 *dst = reinterpret_cast<uint4 *>(out + (int64_t)n * Kp + 32 * kb);
-            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        if (n < N) expand_word(mine, out + (int64_t)n * Kp + 32 * kb);
+    }
+}
+
+__global__ void expand_rows_kernel(const uint32_t *M, int64_t ldm, int rows, int K, uint8_t *out, int Kp,
+                                   const int *run_if)
+{
+    if (run_if && *run_if == 0) return;
+    expand_rows_items(M, ldm, rows, K, out, Kp, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                      (int64_t)gridDim.x * blockDim.x);
+}
+
+__global__ void expand_cols_kernel(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp,
+                                   const int *run_if)
+{
+    if (run_if && *run_if == 0) return;
+    expand_cols_items(M, ldm, K, N, out, Kp, blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32,
+                      (int64_t)gridDim.x * (blockDim.x / 32));
+}
+
+// One launch before squaring `it` of the repeated-squaring closure (M is D x D bits, rw
+// words a row, row stride ld; M2 holds the previous power): flag[it % 3] := M != M2 (did
+// squaring it - 1 change the power?  it = 0: yes); clears flag[(it + 1) % 3] for the next
+// launch; and expands M into both operand layouts of M ⊗ M (A rows, B^T rows).  Once a
+// squaring left the power unchanged (flag[(it - 1) % 3] = 0) the flag stays 0 and nothing
+// is expanded: the later products are skipped.  Blocks [0, nb_cmp) compare, the next
+// nb_rows expand rows, the rest transpose-expand.
+__global__ void square_prep_kernel(const uint32_t *M, const uint32_t *M2, int64_t ld, int D, int rw, uint8_t *Ae,
+                                   uint8_t *Be, int Kp, int *flags, int it, int nb_cmp, int nb_rows)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[(it + 1) % 3] = 0;
+    if (it >= 2 && flags[(it + 2) % 3] == 0) return;          // flag[(it - 1) % 3]: already converged
+    const int b = blockIdx.x;
+    if (b < nb_cmp) {
+        if (it == 0) {
+            if (b == 0 && threadIdx.x == 0) flags[0] = 1;
+            return;
         }
+        const int64_t total = (int64_t)D * rw;
+        bool diff = false;
+        for (int64_t t = b * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nb_cmp * blockDim.x) {
+            const int64_t off = (t / rw) * ld + t % rw;
+            diff |= M[off] != M2[off];
+        }
+        if (__any_sync(0xFFFFFFFFu, diff) && (threadIdx.x & 31) == 0) flags[it % 3] = 1;
+    } else if (b < nb_cmp + nb_rows) {
+        expand_rows_items(M, ld, D, D, Ae, Kp, (b - nb_cmp) * (int64_t)blockDim.x + threadIdx.x,
+                          (int64_t)nb_rows * blockDim.x);
+    } else {
+        const int nbc = gridDim.x - nb_cmp - nb_rows;
+        expand_cols_items(M, ld, D, D, Be, Kp, (b - nb_cmp - nb_rows) * (int64_t)(blockDim.x / 32) + threadIdx.x / 32,
+                          (int64_t)nbc * (blockDim.x / 32));
     }
 }
 
@@ -524,8 +567,7 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
             return fail(SR_EINVAL, "bool_mul (tensor path): the untouched block must lie on the 128 x 256 tile grid");
     }
     uint8_t *Ae = static_cast<uint8_t *>(ws);
-    uint8_t *Be = Ae + (int64_t)a.R * Kp;
-    Be = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(Be) + 255) & ~uintptr_t(255));
+    uint8_t *Be = tc_operand_b(Ae, a.R, Kp);
     const int sms = device_sm_count();
     {
         const int64_t n = (int64_t)a.R * (Kp / 32);
@@ -538,6 +580,38 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
         SR_CUDA_CHECK(cudaGetLastError());
         count_launches(2);
     }
+    return launch_bool_mul_tc_expanded(a, Ae, Be, status, spin_limit, s, max_ctas, run_if);
+}
+
+uint8_t *tc_operand_b(uint8_t *Ae, int64_t R, int Kp)
+{
+    uint8_t *Be = Ae + R * Kp;
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(Be) + 255) & ~uintptr_t(255));
+}
+
+sr_status launch_square_prep(const uint32_t *M, const uint32_t *M2, int64_t ld, int D, int rw, void *ws, int *flags,
+                             int it, cudaStream_t s)
+{
+    const int Kp = (D + tc::BK - 1) / tc::BK * tc::BK;
+    uint8_t *Ae = static_cast<uint8_t *>(ws);
+    uint8_t *Be = tc_operand_b(Ae, D, Kp);
+    const int sms = device_sm_count();
+    const int64_t ncmp = (int64_t)D * rw, nrows = (int64_t)D * (Kp / 32), ncols = (int64_t)((D + 31) / 32) * (Kp / 32);
+    const int nb_cmp = (int)std::max<int64_t>(1, std::min<int64_t>((ncmp + 255) / 256, sms * 4));
+    const int nb_rows = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + 255) / 256, sms * 8));
+    const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, sms * 8));
+    square_prep_kernel<<<nb_cmp + nb_rows + nb_cols, 256, 0, s>>>(M, M2, ld, D, rw, Ae, Be, Kp, flags, it, nb_cmp,
+                                                                  nb_rows);
+    SR_CUDA_CHECK(cudaGetLastError());
+    count_launches();
+    return SR_OK;
+}
+
+sr_status launch_bool_mul_tc_expanded(const BoolArgs &a, uint8_t *Ae, uint8_t *Be, int *status, int spin_limit,
+                                      cudaStream_t s, int max_ctas, const int *run_if)
+{
+    const int Kp = (a.K + tc::BK - 1) / tc::BK * tc::BK;
+    const int sms = device_sm_count();
     CUtensorMap mA, mB;
     if (!make_map(&mA, Ae, a.R, Kp, tc::BM) || !make_map(&mB, Be, a.N, Kp, tc::BN))
         return fail(SR_ECUDA, "bool_mul (tensor path): cannot encode the tensor maps");

@@ -627,28 +627,14 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
     return bool_closure_blocked(T, ldt, D, rw, vec, s);
 }
 
-// *diff := 1 if X and Y (R rows of rw words) differ anywhere (*diff is 0 on entry);
-// clears *clear, the flag the next comparison writes
-__global__ void bool_differs_kernel(const uint32_t *X, const uint32_t *Y, int64_t ld, int R, int rw, int *diff_flag,
-                                    int *clear)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0) *clear = 0;
-    const int64_t total = (int64_t)R * rw;
-    bool diff = false;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t off = (t / rw) * ld + t % rw;
-        diff |= X[off] != Y[off];
-    }
-    if (__any_sync(0xFFFFFFFFu, diff) && (threadIdx.x & 31) == 0) *diff_flag = 1;
-}
-
 // Closure by repeated squaring (Section 2's A ⊗ (I ⊕ A)^(D'-1) identity, D' - 1 rounded up
 // to a power of two): M := I ⊕ A, m squarings, then A ⊗ M, copied back into T.  On the
 // tensor-core path the squarings stop early, on the device: once a squaring leaves M
 // unchanged (M ⊗ M = M) every later one would too, so each squaring runs only if the
-// previous one changed M (a flag written by a comparison kernel and read by the next
-// product's kernels when they start; skipped products leave both buffers equal, so the
-// host's buffer swap stays right).  The result is the same bits either way.
+// previous one changed M.  One launch before each squaring compares M with the previous
+// power, writes that flag and expands M into the product's operands; the product reads the
+// flag when it starts (skipped products leave both buffers equal, so the host's buffer
+// swap stays right).  The result is the same bits either way.
 size_t bool_squaring_workspace(int64_t D, int64_t rw)
 {
     const int64_t ldw = (rw + 3) / 4 * 4;
@@ -688,16 +674,20 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
         return launch_bool_mul(a, v, s);
     };
     if (tcpath)
-        SR_CUDA_CHECK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
-    const int64_t words = (int64_t)D * rw;
-    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, device_sm_count() * 8));
+        SR_CUDA_CHECK(cudaMemsetAsync(flags, 0, 3 * sizeof(int), s));
     for (int it = 0; it < m; ++it) {                                      // M := M ⊗ M
-        // squaring it runs if squaring it-1 changed M (flag (it-1) mod 2)
-        SR_TRY(mul32(M, ldw, M, ldw, M2, tcpath && it > 0 ? flags + ((it - 1) & 1) : nullptr));
         if (tcpath) {
-            bool_differs_kernel<<<cblocks, 256, 0, s>>>(M, M2, ldw, D, rw, flags + (it & 1), flags + ((it + 1) & 1));
-            SR_CUDA_CHECK(cudaGetLastError());
-            count_launches();
+            // one launch tests whether squaring it-1 changed M and expands M for this product,
+            // which runs only if it did (flag it mod 3); two launches a squaring instead of four
+            SR_TRY(launch_square_prep(M, M2, ldw, D, rw, tcws, flags, it, s));
+            BoolArgs a = bool_args(M, M, M2, ldw, D, D, D, rw);
+            a.accumulate = 0;
+            const int Kp = (D + 127) / 128 * 128;
+            uint8_t *Ae = static_cast<uint8_t *>(tcws);
+            SR_TRY(launch_bool_mul_tc_expanded(a, Ae, tc_operand_b(Ae, D, Kp), status, spin_limit, s, 0,
+                                               flags + it % 3));
+        } else {
+            SR_TRY(mul32(M, ldw, M, ldw, M2, nullptr));
         }
         uint32_t *t = M; M = M2; M2 = t;
     }

@@ -117,6 +117,17 @@ bool bool_tc_available();
 // skipped (C untouched) when it is 0 (null: always run)
 sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *status, int spin_limit,
                              cudaStream_t s, int max_ctas = 0, const int *run_if = nullptr);
+// The same product on operands already expanded to e4m3 bytes: Ae (R x Kp, K-major) and Be
+// (N x Kp, B transposed), Kp = K rounded up to 128; no excluded ranges or holes.
+sr_status launch_bool_mul_tc_expanded(const BoolArgs &a, uint8_t *Ae, uint8_t *Be, int *status, int spin_limit,
+                                      cudaStream_t s, int max_ctas = 0, const int *run_if = nullptr);
+uint8_t *tc_operand_b(uint8_t *Ae, int64_t R, int Kp);   // where B^T follows A in a tensor-core workspace
+// Before squaring `it` of the repeated-squaring closure: one launch that sets flags[it % 3]
+// (did squaring it - 1 change M: M != M2; it = 0: 1), clears flags[(it + 1) % 3], and
+// expands M into both operands of M ⊗ M at ws (layout of launch_bool_mul_tc's workspace);
+// after a squaring that changed nothing the flag stays 0 and nothing is expanded.
+sr_status launch_square_prep(const uint32_t *M, const uint32_t *M2, int64_t ld, int D, int rw, void *ws, int *flags,
+                             int it, cudaStream_t s);
 // Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);

@@ -386,12 +386,15 @@ sr_status sr_tune_set(sr_ctx *c, int op, sr_dtype dtype, int64_t D, int choice)
     SR_TRACE("sr_tune_set");
     if (!c)
         return fail(SR_EINVAL, "sr_tune_set: ctx is NULL");
-    const bool ok = (op == SR_OP_ANTIDIST_CLOSURE &&
+    const bool anti = dtype == SR_U8 || dtype == SR_U16 || dtype == SR_U32;
+    const bool boolean = dtype == SR_BOOL_W32 || dtype == SR_BOOL_W64;
+    const bool ok = (op == SR_OP_ANTIDIST_CLOSURE && anti &&
                      (choice == 128 || choice == 256 || choice == 512 || choice == SR_TUNE_PERSISTENT)) ||
-                    (op == SR_OP_BOOL_MUL && choice >= SR_TUNE_BOOL_WORDS && choice <= SR_TUNE_BOOL_TENSOR) ||
-                    (op == SR_OP_ANTIDIST_MUL && (choice == 128 || choice == 64));
+                    (op == SR_OP_BOOL_MUL && boolean && choice >= SR_TUNE_BOOL_WORDS && choice <= SR_TUNE_BOOL_TENSOR) ||
+                    (op == SR_OP_ANTIDIST_MUL && anti && (choice == 128 || choice == 64));
     if (!ok || D <= 0)
-        return fail(SR_EINVAL, "sr_tune_set: op %d, choice %d or D %lld not valid", op, choice, (long long)D);
+        return fail(SR_EINVAL, "sr_tune_set: op %d, dtype %d, choice %d or D %lld not valid", op, (int)dtype, choice,
+                    (long long)D);
     const char *name = op == SR_OP_ANTIDIST_CLOSURE ? "closure" : op == SR_OP_BOOL_MUL ? "bool_mul" : "antidist_mul";
     c->tuned[tune_key(name, dtype, D)] = {(double)choice, 0, 0, 0};
     return tune_persist(c);

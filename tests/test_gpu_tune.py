@@ -122,6 +122,8 @@ def test_single_calls_follow_the_recorded_choice():
             assert np.array_equal(to_host(Zd, np.uint8), want_p), tile
         with pytest.raises(sr.SemiringError):
             sr.sr_tune_set(ctx, sr.SR_OP_ANTIDIST_CLOSURE, sr.SR_U8, D, 300)
+        with pytest.raises(sr.SemiringError):
+            sr.sr_tune_set(ctx, sr.SR_OP_BOOL_MUL, sr.SR_U8, D, sr.SR_TUNE_BOOL_TABLES)   # dtype of another op
     finally:
         sr.sr_destroy(ctx)
 
