@@ -136,9 +136,12 @@ typedef enum {
                                 and a ctx workspace of sr_workspace_query(
                                 SR_OP_ANTIDIST_CLOSURE, dtype, D, 0, ..) bytes; without them the
                                 stream schedule runs. */
-    SR_OPT_CLOSURE_PANEL_SHARE = 6 /* persistent closure: share of each pivot block's phase-3
+    SR_OPT_CLOSURE_PANEL_SHARE = 6, /* persistent closure: share of each pivot block's phase-3
                                 tiles queued before the next pivot block's panels, in 1/256
                                 (0..256, default 128) */
+    SR_OPT_BOOL_SIDE_SMS = 7 /* Boolean closure on the tensor cores (2048-bit blocks): SMs that
+                                phase 3 leaves free for the next diagonal block's update and
+                                squarings running beside it (-1: the default, 32) */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 

@@ -734,8 +734,10 @@ size_t bool_closure_wide_workspace(int64_t D)
 }
 
 sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes,
-                                   int *status, int spin_limit, cudaStream_t s)
+                                   int *status, int spin_limit, cudaStream_t s, int side_sms)
 {
+    if (side_sms < 0) side_sms = kWideSideSms;
+    side_sms = std::min(side_sms, device_sm_count() - 1);
     constexpr int W = kBoolWideBlock, WW = W / 32;
     const int nb = (D + W - 1) / W;
     if (bool_closure_wide_workspace(D) > ws_bytes)
@@ -790,9 +792,9 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void
             p3.hole_r0 = k1; p3.hole_rn = width(kb + 1);
             p3.hole_w0 = kw1; p3.hole_wn = words_of(kb + 1);
         }
-        // beside the diagonal block's squarings, phase 3 leaves kWideSideSms SMs to them
+        // beside the diagonal block's squarings, phase 3 leaves side_sms SMs to them
         SR_TRY(launch_bool_mul_tc(p3, ws, main_bytes, status, spin_limit, s,
-                                  next ? device_sm_count() - kWideSideSms : 0));
+                                  next ? device_sm_count() - side_sms : 0));
         if (next)
             SR_CUDA_CHECK(cudaStreamWaitEvent(s, diag_done[kb + 1], 0));
     }

@@ -243,6 +243,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->closure_share = value;
         return SR_OK;
     }
+    if (option == SR_OPT_BOOL_SIDE_SMS && value >= -1 && value <= 1024) {
+        c->bool_side_sms = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -499,7 +503,7 @@ sr_status bool_closure(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtyp
     if (method == SR_CLOSURE_WARSHALL) {
         if (use_tc_closure(c, D))
             return launch_bool_closure_wide(T32, ldt * u, (int)D, rw, c->ws, c->ws_bytes, c->d_status,
-                                            c->spin_limit, S(stream));
+                                            c->spin_limit, S(stream), c->bool_side_sms);
         return launch_bool_closure_warshall(T32, ldt * u, (int)D, rw, vec, S(stream));
     }
     if (method != SR_CLOSURE_SQUARING)

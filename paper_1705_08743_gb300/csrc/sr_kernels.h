@@ -141,7 +141,7 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
 constexpr int kBoolWideBlock = 2048;
 size_t bool_closure_wide_workspace(int64_t D);
 sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes,
-                                   int *status, int spin_limit, cudaStream_t s);
+                                   int *status, int spin_limit, cudaStream_t s, int side_sms = -1);
 sr_status launch_bool_pack(const uint8_t *dense, int64_t ldd, uint32_t *M, int64_t ldm, int R, int C,
                            int rw, int num_sms, cudaStream_t s);
 sr_status launch_bool_unpack(const uint32_t *M, int64_t ldm, uint8_t *dense, int64_t ldd, int R, int C,
