@@ -85,8 +85,9 @@ typedef struct {
     size_t workspace_bytes;    /* device workspace allocated by sr_create (0: none) */
     int spin_limit;            /* iterations before a device-side wait gives up (0: default) */
     const char *tune_cache;    /* JSON file of autotuned choices (NULL: none); sr_create loads it
-                                  if it exists and was written on a GPU of the same name and SM
-                                  count, and each new tuning rewrites it (see sr_autotune_closure) */
+                                  if it exists, parses, and was written on a GPU of the same name
+                                  and SM count (otherwise it starts with no choices), and each new
+                                  tuning rewrites it (see sr_autotune_closure) */
     int reserved[4];
 } sr_config;
 

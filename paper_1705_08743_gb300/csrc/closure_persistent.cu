@@ -145,6 +145,7 @@ __host__ __device__ __forceinline__ Item step_item(const PcArgs &a, int s, long 
         if (r < nd) return panel_item(a, s + 1, (int)r);
         rest = F + (r - nd);
     }
+    if (P == 0) return {IT_P3, s, 0, 0, -1};               // no tiles outside the cross (not reached)
     const int ip = (int)(rest / P), jp = 2 * (int)(rest % P);
     const int j1 = jp < c0 ? jp : jp + nc;
     const int j2 = jp + 1 < Tr ? (jp + 1 < c0 ? jp + 1 : jp + 1 + nc) : -1;

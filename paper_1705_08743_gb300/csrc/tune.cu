@@ -137,7 +137,7 @@ static sr_status read_cache(sr_ctx *c, const char *path, bool strict)
 {
     FILE *f = fopen(path, "r");
     if (!f) {
-        if (!strict && errno == ENOENT) return SR_OK;          // no cache yet
+        if (!strict) return SR_OK;                             // no cache yet (or not readable): start afresh
         return fail(SR_EINVAL, "tune cache: cannot read %s (%s)", path, strerror(errno));
     }
     std::string text;
@@ -176,8 +176,10 @@ static sr_status read_cache(sr_ctx *c, const char *path, bool strict)
         }
         s.lit(',');
     }
-    if (!ok || version != 1)
+    if (!ok || version != 1) {
+        if (!strict) return SR_OK;                             // at sr_create: an unreadable cache is ignored
         return fail(SR_EINVAL, "tune cache: %s is not a tuning cache this library wrote", path);
+    }
     if (device != device_name(c->device) || (int)sms != device_sm_count()) {
         if (strict)
             return fail(SR_EINVAL, "tune cache: %s was tuned on %s with %d SMs", path, device.c_str(), (int)sms);

@@ -143,6 +143,8 @@ def test_tune_cache_from_another_gpu_is_not_used(tmp_path):
         bad.write_text("{not json")
         with pytest.raises(sr.SemiringError):
             sr.sr_tune_load(ctx, str(bad))
+        ctx3 = sr.sr_create(tune_cache=str(bad))             # a broken cache does not stop sr_create
+        sr.sr_destroy(ctx3)
         # a save followed by a load round-trips
         sr.sr_tune_set(ctx, sr.SR_OP_ANTIDIST_MUL, sr.SR_U8, 5000, 64)
         out = str(tmp_path / "mine.json")
