@@ -136,14 +136,22 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workloads
+CLOSURE_TUNED = {}
+
+
 def closure_ctx(D, sdt, mode="auto"):
     """A context for the anti-distance closure: its workspace holds what the persistent
-    schedule needs (sr_workspace_query), so the library picks that schedule where it
-    is the automatic choice; mode "persistent" / "stream" forces one schedule."""
+    schedule needs (sr_workspace_query).  mode "auto": the library's autotuner times
+    every schedule at this size (stream blocks of 128/256/512, persistent) before any
+    timed step and the closure follows its choice; "persistent" / "stream" force one."""
     import paper_1705_08743_gb300 as sr
     ws = sr.sr_workspace_query(sr.SR_OP_ANTIDIST_CLOSURE, sdt, D) if sdt in (sr.SR_U8, sr.SR_U16) else 0
     ctx = sr.sr_create(workspace_bytes=ws)
     sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_PERSISTENT, {"auto": 1, "persistent": 2, "stream": 0}[mode])
+    if mode == "auto":
+        choice, ms = sr.sr_autotune_closure(ctx, sdt, D, reps=2)
+        CLOSURE_TUNED[D] = {"choice": "persistent" if choice == sr.SR_TUNE_PERSISTENT else f"stream, {choice}-wide blocks",
+                            "best_ms_at_bucket": ms, "bucket": D}
     return ctx
 
 
@@ -1067,7 +1075,8 @@ def run_ours(args, world, rank, local):
                                if persistent else "antidist_closure stream schedule (pivot-block kernel, panel and "
                                                   "phase-3 products)"),
                     "achieved": clo_achieved, "peak": peak, "unit": "Gop/s", "frac": clo_achieved / peak,
-                    "launch_ms": clo_avg, "timing": "CUDA events around the antidist_closure call, encode excluded"}
+                    "launch_ms": clo_avg, "timing": "CUDA events around the antidist_closure call, encode excluded",
+                    "schedule": CLOSURE_TUNED.get(wl.D, "forced by --closure")}
     extra = {}
     if wl.D == 4096 and wl.dtype == "u8" and not args.no_8192:
         extra["closure_8192"] = closure_8192(dev, stream, flush, peak, local, args)
@@ -1140,6 +1149,7 @@ def closure_8192(dev, stream, flush, peak, local, args, reps=5):
     sr.sr_destroy(ctx)
     del Wd, T0, T
     return {"workload": "antidist_closure D=8192 u8 (edge p=0.05, length U{1..31}, seed 1)", "reps": reps,
+            "schedule": CLOSURE_TUNED.get(D, "forced by --closure"),
             "ms": avg, "ms_min": min(ms), "ms_max": max(ms), "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak, "clocks": clk}
 

@@ -140,9 +140,14 @@ typedef enum {
     SR_OPT_CLOSURE_PANEL_SHARE = 6, /* persistent closure: share of each pivot block's phase-3
                                 tiles queued before the next pivot block's panels, in 1/256
                                 (0..256, default 128) */
-    SR_OPT_BOOL_SIDE_SMS = 7 /* Boolean closure on the tensor cores (2048-bit blocks): SMs that
+    SR_OPT_BOOL_SIDE_SMS = 7, /* Boolean closure on the tensor cores (2048-bit blocks): SMs that
                                 phase 3 leaves free for the next diagonal block's update and
                                 squarings running beside it (-1: the default, 32) */
+    SR_OPT_PRODUCT_SPLIT = 8 /* u8/u16 antidist_mul with K >= 1024: when the last wave of CTAs
+                                holds fewer tiles than half the SMs, each of its tiles is
+                                shared by a thread-block cluster of 2-4 CTAs over slices of
+                                K, merged through distributed shared memory (same result;
+                                ⊕ = max is order-free): 0 never, 1 automatic (default) */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 

@@ -36,6 +36,7 @@ SR_OPT_CLOSURE_BLOCK = 4
 SR_OPT_CLOSURE_PERSISTENT = 5
 SR_OPT_CLOSURE_PANEL_SHARE = 6
 SR_OPT_BOOL_SIDE_SMS = 7
+SR_OPT_PRODUCT_SPLIT = 8
 SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES, SR_TUNE_BOOL_TENSOR, SR_TUNE_PERSISTENT = 0, 1, 2, 1
 SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)

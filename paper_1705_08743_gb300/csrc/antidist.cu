@@ -29,7 +29,19 @@ template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
 antidist_mul_kernel(MulArgs p)
 {
-    mul_tiles<KD, BM, BN, BK, TM, TN, VEC>(p, blockIdx.x, gridDim.x);
+    // one tile per CTA; a grid short of the tile count leaves the rest to the split kernel
+    mul_tiles<KD, BM, BN, BK, TM, TN, VEC>(p, blockIdx.x, 1 << 30);
+}
+
+// The last, partial wave of a deep product split along K: cluster c (of n CTAs) computes
+// tile base + c, CTA rank r of it the k-slice [r·kslice, (r+1)·kslice) (kslice a multiple of
+// BK, so every slice starts 16-byte aligned); rank 0 merges and stores.
+template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(MulCfg<KD, BM, BN, BK, TM, TN>::THREADS, MulCfg<KD, BM, BN, BK, TM, TN>::MIN_BLOCKS)
+antidist_mul_split_kernel(MulArgs p, int base, int kslice)
+{
+    mul_tiles<KD, BM, BN, BK, TM, TN, VEC, false, 0, true>(p, base + (int)(blockIdx.x / cluster_size()), 1 << 30,
+                                                           0x7fffffff, kslice);
 }
 
 // Many independent products in one launch (the batched closure's grouped schedule):
@@ -390,17 +402,69 @@ static sr_status launch_mul_cfg(const MulArgs &a, bool vec, cudaStream_t s)
         return fail(SR_EINVAL, "antidist_mul: too many tiles (%lld)", (long long)tiles);
     auto kern = vec ? antidist_mul_kernel<KD, BM, BN, BK, TM, TN, true>
                     : antidist_mul_kernel<KD, BM, BN, BK, TM, TN, false>;
+    constexpr bool kSplits = TN == 16;                  // the 128×128 tiles of deep products
     static bool attr[2][kMaxDevices] = {};
+    static int slots[kMaxDevices] = {}, sm_count[kMaxDevices] = {};
     SR_DEVICE_SLOT(dev);
     if (!attr[vec][dev]) {
         SR_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        if constexpr (kSplits) {
+            auto split = vec ? antidist_mul_split_kernel<KD, BM, BN, BK, TM, TN, true>
+                             : antidist_mul_split_kernel<KD, BM, BN, BK, TM, TN, false>;
+            SR_CUDA_CHECK(cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+        }
+        int per_sm = 0, sms = 0, d = 0;
+        SR_CUDA_CHECK(cudaGetDevice(&d));
+        SR_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, Cfg::SMEM));
+        SR_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d));
+        slots[dev] = per_sm * sms;
+        sm_count[dev] = sms;
         attr[vec][dev] = true;
     }
-    // one tile per CTA: the hardware block scheduler balances a sparse last wave better than
-    // a persistent grid or smaller tail tiles on a second stream (both measured slower)
-    kern<<<(unsigned)tiles, Cfg::THREADS, Cfg::SMEM, s>>>(a);
-    SR_CUDA_CHECK(cudaGetLastError());
-    count_launches();
+    // One tile per CTA: the hardware block scheduler balances a sparse last wave better than
+    // a persistent grid or smaller tail tiles on a second stream (both measured slower).
+    // A CTA alone on an SM runs its tile about as fast as the SM runs three (the k-loop has
+    // ILP enough), so a last wave of up to one tile per SM costs a whole tile time however
+    // few its tiles.  When the last wave is that sparse, its tiles go to clusters of split_k
+    // CTAs over slices of K instead, with split_k as large as keeps one CTA per SM (a 6144³
+    // u8 product on GB300: 2304 tiles on 456 slots leave 24, split 4 ways: 6.70 -> 6.44 ms).
+    // Where split CTAs would share SMs the split gains nothing (4096³: 112 tail tiles;
+    // 2.00 ms unsplit, 2.03 ms as 112 clusters of 4).
+    const int nkt = (a.K + BK - 1) / BK;
+    const int tail = slots[dev] > 0 ? (int)(tiles % slots[dev]) : 0;
+    int split_k = 0;
+    if (kSplits && a.K >= 1024 && a.skip_tile < 0 && a.rskipw == 0 && a.cskipw == 0 && tail > 0 && a.split)
+        split_k = std::min(std::min(4, sm_count[dev] / tail), nkt / 4);
+    if (split_k < 2) {
+        kern<<<(unsigned)tiles, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+        SR_CUDA_CHECK(cudaGetLastError());
+        count_launches();
+        return SR_OK;
+    }
+    if (tiles > tail) {
+        kern<<<(unsigned)(tiles - tail), Cfg::THREADS, Cfg::SMEM, s>>>(a);
+        SR_CUDA_CHECK(cudaGetLastError());
+        count_launches();
+    }
+    if constexpr (kSplits) {
+        auto split = vec ? antidist_mul_split_kernel<KD, BM, BN, BK, TM, TN, true>
+                         : antidist_mul_split_kernel<KD, BM, BN, BK, TM, TN, false>;
+        const int kslice = (nkt + split_k - 1) / split_k * BK;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(tail * split_k));
+        lc.blockDim = dim3(Cfg::THREADS);
+        lc.dynamicSmemBytes = Cfg::SMEM;
+        lc.stream = s;
+        cudaLaunchAttribute la[1];
+        la[0].id = cudaLaunchAttributeClusterDimension;
+        la[0].val.clusterDim.x = (unsigned)split_k;
+        la[0].val.clusterDim.y = 1;
+        la[0].val.clusterDim.z = 1;
+        lc.attrs = la;
+        lc.numAttrs = 1;
+        SR_CUDA_CHECK(cudaLaunchKernelEx(&lc, split, a, (int)(tiles - tail), kslice));
+        count_launches();
+    }
     return SR_OK;
 }
 

@@ -86,10 +86,71 @@ __device__ __forceinline__ void tile_sync()
         asm volatile("bar.sync %0, 128;\n" ::"n"(SYNC) : "memory");
 }
 
+// Thread-block cluster helpers (distributed shared memory)
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size()
+{
+    uint32_t n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(n));
+    return n;
+}
+// every thread of every CTA of the cluster: writes before it are visible to reads after it
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// the shared::cluster address of the same shared-memory word in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_map(const void *p, uint32_t rank)
+{
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n"
+                 : "=r"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return a;
+}
+// x[0..7] := lanewise max (unsigned 16-bit lanes) of x and the two 16-byte words at
+// shared::cluster address a and a + stride; load and max in one block, so that only the
+// words in flight add to the registers the accumulators hold
+__device__ __forceinline__ void cluster_max8(uint32_t (&x)[8], uint32_t a, uint32_t stride)
+{
+    asm volatile("{\n"
+                 ".reg .b32 t<8>;\n"
+                 ".reg .u32 a1;\n"
+                 "add.u32 a1, %8, %9;\n"
+                 "ld.shared::cluster.v4.u32 {t0, t1, t2, t3}, [%8];\n"
+                 "ld.shared::cluster.v4.u32 {t4, t5, t6, t7}, [a1];\n"
+                 "max.u16x2 %0, %0, t0;\n"
+                 "max.u16x2 %1, %1, t1;\n"
+                 "max.u16x2 %2, %2, t2;\n"
+                 "max.u16x2 %3, %3, t3;\n"
+                 "max.u16x2 %4, %4, t4;\n"
+                 "max.u16x2 %5, %5, t5;\n"
+                 "max.u16x2 %6, %6, t6;\n"
+                 "max.u16x2 %7, %7, t7;\n"
+                 "}\n"
+                 : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(x[7])
+                 : "r"(a), "r"(stride)
+                 : "memory");
+}
+
 // Tiles tile0, tile0 + stride, ... below tile_end of the product p (one CTA, or its first 128
 // threads with SYNC > 0; shared memory as sized by MulCfg).
-template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC, bool CG = false, int SYNC = 0>
-__device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int stride, int tile_end = 0x7fffffff)
+//
+// SPLIT: the CTAs of a thread-block cluster share one tile, CTA rank r over the slice
+// [r·kslice, (r+1)·kslice) of K (kslice a multiple of BK; C joins at rank 0 only).  After
+// the k-loop every CTA leaves its accumulators in its own shared memory; rank 0 reads them
+// back, taking the lanewise max with the other ranks' through distributed shared memory
+// (⊕ = max is associative and commutative, so the slices may merge in any order), and
+// alone runs the epilogue.  One tile per CTA, no skipped tiles.
+template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC, bool CG = false, int SYNC = 0,
+          bool SPLIT = false>
+__device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int stride, int tile_end = 0x7fffffff,
+                                          int kslice = 0)
 {
     using Cfg = MulCfg<KD, BM, BN, BK, TM, TN>;
     using E = typename KD::elem;
@@ -125,7 +186,11 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
         trow = g0 + w % gm;
         tcol = w / gm;
     };
-    const int nkt = (p.K + BK - 1) / BK;
+    const uint32_t crank = SPLIT ? cluster_rank() : 0u;
+    const int kbeg = SPLIT ? (int)crank * kslice : 0;
+    const int kend = SPLIT ? min(p.K, kbeg + kslice) : p.K;
+    const bool accum = p.accumulate && crank == 0;
+    const int nkt = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;   // an empty slice leaves the identity
 
     // tiles tile0, tile0 + stride, ... of the row-major tile grid (one per CTA when stride >= tiles)
     // skip_tile names a block of the 128x128 tile grid, which every tile shape here nests in.
@@ -153,8 +218,8 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
             const int ch = tid + u * THREADS;
             const int i = ch % BM, kc = ch / BM;
             const int r = row0 + i;
-            ra[u] = r < p.R ? load_chunk<E, VEC, CG>(A, p.lda, remap(r, p.rskip0, p.rskipw), k0 + kc * CH,
-                                                 0x7fffffff, p.K)
+            ra[u] = r < p.R ? load_chunk<E, VEC, CG>(A, p.lda, remap(r, p.rskip0, p.rskipw), kbeg + k0 + kc * CH,
+                                                 0x7fffffff, kend)
                             : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
@@ -163,9 +228,9 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
             const int jc = ch % (BN / CH), kr = ch / (BN / CH);
             const int c = col0 + jc * CH;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (c < p.N && k0 + kr < p.K) {   // the chunk never straddles an excluded range
+            if (c < p.N && kbeg + k0 + kr < kend) {   // the chunk never straddles an excluded range
                 const int pc = remap(c, p.cskip0, p.cskipw);
-                v = load_chunk<E, VEC, CG>(B, p.ldb, k0 + kr, pc, p.K, pc + (p.N - c));
+                v = load_chunk<E, VEC, CG>(B, p.ldb, kbeg + k0 + kr, pc, kend, pc + (p.N - c));
             }
             rb[u] = v;
         }
@@ -233,7 +298,7 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
         int trow, tcol;
         tile_rc(tile, trow, tcol);
         const int row0 = trow * BM, col0 = tcol * BN;
-        if (p.accumulate) cprefetch(row0, col0);
+        if (accum) cprefetch(row0, col0);
         gload(row0, col0, 0);
     }
 
@@ -294,8 +359,42 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
             tile_sync<SYNC>();
         }
 
+        if constexpr (SPLIT) {
+            // the k-loop's staging is free after its last barrier: the partial goes there,
+            // word j of thread t at [j / 4][t] (conflict-free 16-byte rows)
+            static_assert(Cfg::SMEM - (size_t)BM * BN * sizeof(E) >= (size_t)TM * NP * 4 * THREADS,
+                          "the partial tile fits in the operand staging");
+            // (rank 0's too: its accumulators are rebuilt row by row, which keeps the merge
+            // within the k-loop's register budget)
+            uint4 *part = reinterpret_cast<uint4 *>(smem);
+            const uint32_t rank = crank;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int g = 0; g < NP / 4; ++g)
+                    part[(i * (NP / 4) + g) * THREADS + tid] =
+                        make_uint4(acc[i][4 * g], acc[i][4 * g + 1], acc[i][4 * g + 2], acc[i][4 * g + 3]);
+            cluster_sync();
+            if (rank == 0) {
+                static_assert(NP == 8, "one row of a thread's accumulators is two 16-byte words");
+                const uint32_t n = cluster_size();
+#pragma unroll
+                for (int i = 0; i < TM; ++i) {
+                    const uint4 v0 = part[(2 * i) * THREADS + tid], v1 = part[(2 * i + 1) * THREADS + tid];
+                    uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    for (uint32_t r = 1; r < n; ++r)
+                        cluster_max8(x, cluster_map(part + (2 * i) * THREADS + tid, r), (uint32_t)THREADS * 16u);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[i][u] = x[u];
+                }
+            }
+            cluster_sync();                        // the other ranks' shared memory outlives the reads
+            if (rank != 0)
+                continue;
+        }
+
         // ---- epilogue: ⊕ with C (prefetched into sC), store
-        if (p.accumulate) {
+        if (accum) {
             asm volatile("cp.async.wait_group 0;\n" ::);
             tile_sync<SYNC>();
         }
@@ -321,7 +420,7 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
 #pragma unroll
                     for (int u = 0; u < 4; ++u) q[u] = acc[i][g * 4 + u];
                 }
-                if (p.accumulate) {
+                if (accum) {
                     const uint32_t *crow = reinterpret_cast<const uint32_t *>(sC + li * CROW);
                     if (sizeof(E) == 1) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(crow + lc / 4);
@@ -354,7 +453,7 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
                 }
             }
         }
-        if (p.accumulate) {
+        if (accum) {
             tile_sync<SYNC>();                                   // sC is free again
             if (next < tiles) cprefetch(nrow0, ncol0);         // lands during the next tile's k-loop
         }

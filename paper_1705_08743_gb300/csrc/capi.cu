@@ -247,6 +247,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->bool_side_sms = value;
         return SR_OK;
     }
+    if (option == SR_OPT_PRODUCT_SPLIT && (value == 0 || value == 1)) {
+        c->product_split = value;
+        return SR_OK;
+    }
     return fail(SR_EINVAL, "sr_set_option: unknown option %d or value %d", option, value);
 }
 
@@ -355,6 +359,7 @@ sr_status antidist_mul(sr_ctx *ctx, const void *A, int64_t lda, const void *B, i
     a.rskip0 = a.cskip0 = 0x7fffffff;
     a.rskipw = a.cskipw = 0;
     a.skip_tile = -1;
+    a.split = ctx ? ctx->product_split : 1;
     const bool vec = vec_ok(dtype, {{A, lda}, {B, ldb}, {C, ldc}});
     int tile = 128;     // the autotuner's tile side for this size, if it recorded one
     tune_lookup(ctx, tune_key("antidist_mul", dtype, std::max(R, std::max(K, N))), &tile);

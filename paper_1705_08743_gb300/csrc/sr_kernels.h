@@ -54,6 +54,7 @@ struct MulArgs {
     int cskip0, cskipw;
     int skip_tile = -1;        // a tile (row-major index, 128x128 tiles) left untouched, or -1
     int group_m = 0;           // tile order: 0 row-major; g > 0 column-major within groups of g tile rows
+    int split = 1;             // a partial last wave of a deep product may split along K (u8/u16)
 };
 
 // tiles: 0 = 128x128 CTA tiles (throughput; u32: 128x64), 1 = 64x64 (latency: more CTAs for

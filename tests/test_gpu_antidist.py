@@ -100,6 +100,52 @@ def test_mul_more_than_one_wave(dt):
 
 
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("shape", [(1000, 1100, 1000), (2816, 1024, 2704)])
+def test_mul_deep_last_wave_split_along_k(dt, shape):
+    """Deep products (K >= 1024) whose last wave of CTAs is partial: its tiles are shared
+    by thread-block clusters over slices of K and merged through distributed shared memory
+    (64 tiles, all split two ways, ragged R, N and K; 22 x 22 tiles: for u8 one full wave
+    of 456 CTAs plus a tail of 28 split four ways, for u16 a last wave of 180 tiles, too
+    full to split).  Equal to the oracle with and without accumulation, and to the unsplit
+    launch (SR_OPT_PRODUCT_SPLIT = 0), which takes one launch where the split takes two."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    rng = np.random.default_rng(shape[0] + shape[1])
+    S = S_OF[dt]
+    R, K, N = shape
+    A, B = rand_anti(rng, R, K, dt, 0.3), rand_anti(rng, K, N, dt, 0.3)
+    C0 = rand_anti(rng, R, N, dt, 0.2)
+    want0, want1 = oracle.mul(A, B, S), oracle.mul(A, B, S, C=C0)
+    ctx = sr.sr_create()
+    try:
+        Ad, Bd = to_dev(A), to_dev(B)
+        launches = {}
+        for split in (1, 0):
+            sr.sr_set_option(ctx, sr.SR_OPT_PRODUCT_SPLIT, split)
+            for C_init, want in ((None, want0), (C0, want1)):
+                Cd = to_dev(np.zeros((R, N), dt) if C_init is None else C_init)
+                torch.cuda.synchronize()
+                n0 = sr.sr_kernel_launches()
+                sr.antidist_mul(ctx, Ad, Ad.shape[1], Bd, Bd.shape[1], Cd, Cd.shape[1], R, K, N,
+                                sr_dtype_of(dt), 0 if C_init is None else 1)
+                torch.cuda.synchronize()
+                launches[split] = sr.sr_kernel_launches() - n0
+                assert np.array_equal(to_host(Cd, dt)[:, :N], want), (split, C_init is None)
+        tiles = ((R + 127) // 128) * ((N + 127) // 128)
+        # resident CTAs per SM: u8 3 (registers), u16 2 (112 KB of shared memory each); the
+        # tail splits at least two ways while that keeps one split CTA per SM
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        slots = (3 if dt == np.uint8 else 2) * sms
+        tail = tiles % slots
+        assert launches[0] == 1
+        assert launches[1] == (2 if tiles > slots and 0 < 2 * tail <= sms else 1)
+        with pytest.raises(sr.SemiringError):
+            sr.sr_set_option(ctx, sr.SR_OPT_PRODUCT_SPLIT, 2)
+    finally:
+        sr.sr_destroy(ctx)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 def test_closure_24_pivot_blocks(dt):
     """D = 3072: 24 pivot blocks, each phase 3 more than one wave of 128x128 tiles, with
     the look-ahead chain of the next block running beside it on the side stream."""
