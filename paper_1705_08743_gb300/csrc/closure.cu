@@ -24,7 +24,8 @@
 
 namespace sr {
 
-// Side stream (high priority) and a per-thread pool of events for the look-ahead.
+// Side streams (0..2 high priority, kPeerStream the lowest, as the caller's default
+// stream) and a per-thread pool of events for the look-ahead.
 cudaStream_t side_stream(int i)
 {
     static cudaStream_t st[kMaxDevices][kSideStreams] = {};
@@ -36,7 +37,7 @@ cudaStream_t side_stream(int i)
     if (!st[dev][i]) {
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&st[dev][i], cudaStreamNonBlocking, hi) != cudaSuccess)
+        if (cudaStreamCreateWithPriority(&st[dev][i], cudaStreamNonBlocking, i == kPeerStream ? lo : hi) != cudaSuccess)
             st[dev][i] = nullptr;
     }
     return st[dev][i];
@@ -210,22 +211,63 @@ sr_status closure_two_streams(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
 // only panel kb, the diagonal block after P, and its own row or column.  The side work
 // for kb+1 starts once main's phase 3 of kb-1 (the last writer of block row and column
 // kb+1) and the panels of kb are done; main's phase 3 of kb+1 waits for both panels.
+//
+// With a peer stream sb, "main" is two streams: phase 3 of every block is split at a
+// tile-row boundary, the upper rows on s and the lower rows on sb.  Each half of pass
+// kb+1 needs only the same half of pass kb (its own C tiles) and the panels of kb+1, so
+// the two streams run their passes independently, and the drain and launch gap at the
+// end of one stream's pass are filled by the other stream's CTAs.  The side work waits
+// for both halves.  One half's pass kb+1 may update row or column block kb (outside its
+// band) while the other half's pass kb still reads that block as its panel.  The read
+// sees old or new entries, and either gives the same fixed point: a new entry is the old
+// one ⊕ weights of paths through block kb+1, all of which the closure holds, and ⊗ is
+// monotone, so every value stays between the blocked loop's and the closure's.
+// Two main streams from this much phase-3 work per pass (128×128 tiles × W / 128 × entry
+// bytes).  GB300 closure times, one stream -> two: u8 D = 4608 3.83 -> 3.41 ms, 5120
+// 4.90 -> 4.54, 5632 6.27 -> 5.65, 6144 7.82 -> 7.30, 8192 (W = 256) 16.51 -> 16.26; u16
+// D = 4096 5.00 -> 4.74.  At u8 D = 4096 (900 tiles a pass, 1.97 waves of 456 CTAs: the
+// passes' tails are small already) and below, no change or up to 1.5 % slower.
+constexpr int64_t kPeerMinWork = 1000;
+
 template <class E>
 sr_status closure_look_ahead(void *T, int64_t ldt, int D, int W, bool vec, sr_dtype dt, cudaStream_t s,
-                             cudaStream_t sp, cudaStream_t sr_, cudaStream_t sc)
+                             cudaStream_t sp, cudaStream_t sr_, cudaStream_t sc, cudaStream_t sb)
 {
     const int nb = (D + W - 1) / W;
     auto width = [&](int kb) { return std::min(W, D - kb * W); };
+    {   // phase-3 work per pass in 128-deep u8 tiles; below kPeerMinWork one stream
+        const int64_t tn = (D - 2 * W + PB - 1) / PB;
+        if (tn * tn * (W / PB) * (int64_t)sizeof(E) < kPeerMinWork) sb = nullptr;
+    }
     // strips and panels of the next block: 64x64 tiles for 128-wide blocks (enough CTAs
     // for a 128-row panel), 128x128 tiles for wider ones (more work per staged byte;
     // GB300, u8 D = 8192, W = 256: 16.4 ms against 17.0 ms with 64x64 tiles)
     const int side_tiles = W > PB ? 0 : 1;
     std::vector<cudaEvent_t> *ev = nullptr;
-    SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
-    cudaEvent_t *main_done = ev->data();              // [kb]: main's phase 3 of kb
+    SR_TRY(event_pool(5 * (size_t)nb + 6, ev));
+    cudaEvent_t *main_done = ev->data();              // [kb]: main's phase 3 of kb (upper rows with sb)
     cudaEvent_t *pivot_done = main_done + nb + 1;     // [kb]: block (kb, kb) closed
     cudaEvent_t *rowp_done = pivot_done + nb + 1;     // [kb]: row panel of kb
     cudaEvent_t *colp_done = rowp_done + nb + 1;      // [kb]: column panel of kb
+    cudaEvent_t *low_done = colp_done + nb + 1;       // [kb]: sb's lower rows of phase 3 of kb; [nb]: join
+    // phase 3 of block kb over logical rows [r0, r1) of the D - ex rows outside the band
+    // [k0, k0 + ex): the upper part keeps the band's exclusion, the lower part starts at
+    // its first physical row and excludes the band only if it still lies below
+    auto phase3_rows = [&](int k0, int bw, int ex, int r0, int r1, cudaStream_t st) -> sr_status {
+        if (r1 <= r0)
+            return SR_OK;
+        const int p0 = r0 < k0 ? r0 : r0 + ex;                  // physical first row
+        const int rs0 = r0 < k0 ? k0 - r0 : NONE, rsw = r0 < k0 ? ex : 0;
+        return phase3<E>(T, ldt, k0, bw, p0, r1 - r0, rs0, rsw, 0, D - ex, k0, ex, dt, vec, st, 0);
+    };
+    auto phase3_main = [&](int k0, int bw, int ex) -> sr_status {
+        const int rows = D - ex;
+        if (!sb)
+            return phase3_rows(k0, bw, ex, 0, rows, s);
+        const int split = ((rows + PB - 1) / PB / 2) * PB;      // a tile-row boundary
+        SR_TRY(phase3_rows(k0, bw, ex, 0, split, s));
+        return phase3_rows(k0, bw, ex, split, rows, sb);
+    };
     SR_TRY(close_diagonal<E>(T, ldt, D, W, 0, width(0), -1, 0, vec, dt, s));
     SR_TRY(phase2<E>(T, ldt, D, 0, width(0), true, dt, vec, s));
     SR_TRY(phase2<E>(T, ldt, D, 0, width(0), false, dt, vec, s));
@@ -235,16 +277,21 @@ sr_status closure_look_ahead(void *T, int64_t ldt, int D, int W, bool vec, sr_dt
         const int k0 = kb * W, bw = width(kb);
         const bool next = kb + 1 < nb;
         const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;     // rows/columns left out
-        if (kb > 0) {
-            SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
-            SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
+        // s may be the legacy default stream, whose handle is null: only sb's null means absent
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, rowp_done[kb], 0));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, colp_done[kb], 0));
+        if (sb) {                             // kb = 0: sb forks from s here
+            SR_CUDA_CHECK(cudaStreamWaitEvent(sb, rowp_done[kb], 0));
+            SR_CUDA_CHECK(cudaStreamWaitEvent(sb, colp_done[kb], 0));
         }
-        SR_TRY(phase3<E>(T, ldt, k0, bw, 0, D - ex, k0, ex, 0, D - ex, k0, ex, dt, vec, s, 0));
+        SR_TRY(phase3_main(k0, bw, ex));
         if (!next)
             break;
         SR_CUDA_CHECK(cudaEventRecord(main_done[kb], s));
+        if (sb) SR_CUDA_CHECK(cudaEventRecord(low_done[kb], sb));
         for (cudaStream_t x : {sp, sr_, sc}) {
             if (kb > 0) SR_CUDA_CHECK(cudaStreamWaitEvent(x, main_done[kb - 1], 0));
+            if (kb > 0 && sb) SR_CUDA_CHECK(cudaStreamWaitEvent(x, low_done[kb - 1], 0));
             SR_CUDA_CHECK(cudaStreamWaitEvent(x, rowp_done[kb], 0));
             SR_CUDA_CHECK(cudaStreamWaitEvent(x, colp_done[kb], 0));
         }
@@ -259,6 +306,10 @@ sr_status closure_look_ahead(void *T, int64_t ldt, int D, int W, bool vec, sr_dt
         SR_CUDA_CHECK(cudaStreamWaitEvent(sc, pivot_done[kb + 1], 0));
         SR_TRY(phase2<E>(T, ldt, D, k1, bwn, false, dt, vec, sc, side_tiles));
         SR_CUDA_CHECK(cudaEventRecord(colp_done[kb + 1], sc));
+    }
+    if (sb) {                                 // join: s waits for sb's last pass
+        SR_CUDA_CHECK(cudaEventRecord(low_done[nb], sb));
+        SR_CUDA_CHECK(cudaStreamWaitEvent(s, low_done[nb], 0));
     }
     return SR_OK;
 }
@@ -296,7 +347,7 @@ sr_status closure_impl(void *T, int64_t ldt, int D, bool vec, sr_dtype dt, cudaS
             return launch_antidist_pivot(T, ldt, D, 0, -1, dt, vec, s);
         return closure_two_streams<E>(T, ldt, D, vec, dt, s, sp);
     }
-    return closure_look_ahead<E>(T, ldt, D, W, vec, dt, s, sp, sr_, sc);
+    return closure_look_ahead<E>(T, ldt, D, W, vec, dt, s, sp, sr_, sc, side_stream(kPeerStream));
 }
 
 }  // namespace

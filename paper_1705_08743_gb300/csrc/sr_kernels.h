@@ -36,8 +36,11 @@ std::string tune_key(const char *op, sr_dtype t, int64_t D);
 bool tune_lookup(const sr_ctx *c, const std::string &key, int *choice);
 sr_status tune_load_config(sr_ctx *c, const char *path);   // at sr_create; a missing file is fine
 sr_status tune_persist(const sr_ctx *c);                     // rewrite the cache, if the ctx has one
-constexpr int kSideStreams = 3;
-cudaStream_t side_stream(int i = 0);   // per-device high-priority streams for look-ahead work (may be null)
+constexpr int kSideStreams = 4;
+// per-device streams for look-ahead work (may be null): 0..2 high priority, 3 (kPeerStream)
+// default priority, a second main stream beside the caller's
+constexpr int kPeerStream = 3;
+cudaStream_t side_stream(int i = 0);
 sr_status event_pool(size_t n, std::vector<cudaEvent_t> *&out);   // per-thread, per-device events
 
 // Product C := (accumulate ? C : 0) ⊕ A ⊗ B over logical R×K×N.  Rows of A/C

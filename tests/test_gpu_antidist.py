@@ -194,6 +194,19 @@ def test_closure_many_pivot_blocks(dt, D):
         assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
 
 
+@pytest.mark.parametrize("D,dt", [(4700, np.uint8), (3700, np.uint16)])
+def test_closure_phase3_on_two_main_streams(D, dt):
+    """Look-ahead schedules with enough phase-3 work per pass that each pass is split at
+    a tile-row boundary over the caller's stream and a peer stream (u8 D=4700: 35 x 35
+    tiles a pass; u16 D=3700: 27 x 27 two-byte tiles), with a ragged last block: equal
+    to the oracle's Warshall/Floyd closure, for long sparse paths and for dense input."""
+    rng = np.random.default_rng(D)
+    S = S_OF[dt]
+    for dens, lo in [(3.0 / D, S - S // 8), (0.05, 1)]:
+        A = rand_anti(rng, D, D, dt, dens, lo)
+        assert np.array_equal(gpu_closure(A), oracle.warshall(A, S)), (dens, lo)
+
+
 _WANT = {}
 
 
@@ -346,6 +359,7 @@ def test_closure_captured_in_cuda_graph(D, dt):
         T.copy_(src)
         sr.antidist_closure(None, T, D, D, sr_dtype_of(dt), s.cuda_stream)      # warm-up outside capture
     torch.cuda.synchronize()
+    assert np.array_equal(to_host(T, dt), want)                                 # the eager run, too
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         T.copy_(src)
