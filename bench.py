@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-8192", action="store_true", help="default workload: skip the D=8192 closure timing")
     ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched (config 4) summary")
+    ap.add_argument("--no-bool", action="store_true",
+                    help="default workload: skip the Boolean closure (config 3, D=16384) summary")
     ap.add_argument("--closure", default="auto", choices=["auto", "persistent", "stream"],
                     help="anti-distance closure schedule (auto: the library's choice with the workspace it asks for)")
     ap.add_argument("--tuning", default="", help="batched workloads: cluster,threshold,ctas_per_sm (skips autotune)")
@@ -1082,6 +1084,8 @@ def run_ours(args, world, rank, local):
         extra["closure_8192"] = closure_8192(dev, stream, flush, peak, local, args)
     if wl.D == 4096 and wl.dtype == "u8" and not args.no_batched:
         extra["batched_cfg4"] = batched_summary(dev, stream, flush, args)
+    if wl.D == 4096 and wl.dtype == "u8" and not args.no_bool:
+        extra["bool_closure_cfg3"] = bool_closure_summary(dev, stream, flush)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1152,6 +1156,47 @@ def closure_8192(dev, stream, flush, peak, local, args, reps=5):
             "schedule": CLOSURE_TUNED.get(D, "forced by --closure"),
             "ms": avg, "ms_min": min(ms), "ms_max": max(ms), "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak, "clocks": clk}
+
+
+def bool_closure_summary(dev, stream, flush, steps=5):
+    """Config 3 (Boolean transitive closure, D=16384, 64-bit words) beside the default
+    step: pack + blocked Warshall with phase 3 on the tensor cores, timed `steps` times
+    with the L2 flushed, against the fp8 tensor-pipe peak probed now (D^3 multiply-adds
+    of 0/1 e4m3 operands = 2 D^3 flops)."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    wl = CfgBool("cfg3")
+    A, _ = wl.host_inputs()
+    wl.setup_device(A, None, dev)
+    del A
+    with torch.cuda.stream(stream):
+        f8 = sr.sr_peak_probe(sr.SR_PEAK_TC_F8, iters=65536, blocks_per_sm=1, stream=stream.cuda_stream)[2] / 1e12
+        for _ in range(2):
+            wl.step(stream)
+    torch.cuda.synchronize()
+    ev = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wl.step(stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    sr.sr_stream_status(wl.wctx, stream.cuda_stream)
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    avg = sum(ms) / len(ms)
+    tflops = 2.0 * wl.ops / (avg * 1e-3) / 1e12
+    out = {"workload": wl.name, "steps": steps, "ms": avg, "ms_min": ms[0], "ms_max": ms[-1],
+           "bound": "tensor", "achieved": tflops, "peak": f8, "unit": "TFLOP/s", "frac": tflops / f8,
+           "peak_source": "measured now: tcgen05.mma kind::f8f6f4 issue stream on all SMs (SR_PEAK_TC_F8)",
+           "l2": "flushed before each step"}
+    sr.sr_destroy(wl.ctx)
+    sr.sr_destroy(wl.wctx)
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_summary(dev, stream, flush, args, steps=5):
