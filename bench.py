@@ -152,7 +152,8 @@ def closure_ctx(D, sdt, mode="auto"):
     sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_PERSISTENT, {"auto": 1, "persistent": 2, "stream": 0}[mode])
     if mode == "auto":
         choice, ms = sr.sr_autotune_closure(ctx, sdt, D, reps=2)
-        CLOSURE_TUNED[D] = {"choice": "persistent" if choice == sr.SR_TUNE_PERSISTENT else f"stream, {choice}-wide blocks",
+        name = {sr.SR_TUNE_PERSISTENT: "persistent", sr.SR_TUNE_FUSED: "fused passes (one launch per pivot block)"}
+        CLOSURE_TUNED[D] = {"choice": name.get(choice, f"stream, {choice}-wide blocks"),
                             "best_ms_at_bucket": ms, "bucket": D}
     return ctx
 
@@ -1071,11 +1072,12 @@ def run_ours(args, world, rank, local):
     with torch.cuda.stream(stream):
         sr.antidist_closure(wl.ctx, wl.T, wl.D, wl.D, wl.sdt, stream.cuda_stream)
     torch.cuda.synchronize()
-    persistent = sr.sr_kernel_launches() - n0 == 1
-    roof_closure = {"bound": "alu",
-                    "kernel": (f"antidist_closure_persistent_kernel<Kind{wl.dtype.upper()}> (whole closure, one launch)"
-                               if persistent else "antidist_closure stream schedule (pivot-block kernel, panel and "
-                                                  "phase-3 products)"),
+    nl = sr.sr_kernel_launches() - n0
+    nb = (wl.D + 127) // 128
+    kernel = ("antidist_closure stream schedule (pivot-block kernel, panel and phase-3 products)" if nl not in (1, nb + 1)
+              else f"antidist_closure_persistent_kernel<Kind{wl.dtype.upper()}> (whole closure, one launch)" if nl == 1
+              else f"closure_fused_kernel<Kind{wl.dtype.upper()}> (one launch per pivot block)")
+    roof_closure = {"bound": "alu", "kernel": kernel,
                     "achieved": clo_achieved, "peak": peak, "unit": "Gop/s", "frac": clo_achieved / peak,
                     "launch_ms": clo_avg, "timing": "CUDA events around the antidist_closure call, encode excluded",
                     "schedule": CLOSURE_TUNED.get(wl.D, "forced by --closure")}

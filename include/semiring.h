@@ -143,11 +143,18 @@ typedef enum {
     SR_OPT_BOOL_SIDE_SMS = 7, /* Boolean closure on the tensor cores (2048-bit blocks): SMs that
                                 phase 3 leaves free for the next diagonal block's update and
                                 squarings running beside it (-1: the default, 32) */
-    SR_OPT_PRODUCT_SPLIT = 8 /* u8/u16 antidist_mul with K >= 1024: when the last wave of CTAs
+    SR_OPT_PRODUCT_SPLIT = 8, /* u8/u16 antidist_mul with K >= 1024: when the last wave of CTAs
                                 holds fewer tiles than half the SMs, each of its tiles is
                                 shared by a thread-block cluster of 2-4 CTAs over slices of
                                 K, merged through distributed shared memory (same result;
                                 ⊕ = max is order-free): 0 never, 1 automatic (default) */
+    SR_OPT_CLOSURE_FUSED = 9 /* u8/u16 anti-distance closure with one launch per 128-wide pivot
+                                block, the next block's phases 1-2 taken as work items beside
+                                the current phase 3 (bounded waits as SR_OPT_SPIN_LIMIT):
+                                0 never, 1 automatic (default), 2 whenever possible.  Needs
+                                16-byte aligned rows and a ctx workspace of
+                                sr_workspace_query(SR_OP_ANTIDIST_CLOSURE, ..) bytes;
+                                without them the stream schedule runs. */
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 
@@ -165,23 +172,27 @@ sr_status sr_shard_rows(int64_t R, int world, int rank, int64_t align, int64_t *
 /* ---------------------------------------------------------------- autotuner */
 
 /* Choices the autotuner records (sr_tune_get / sr_tune_set):
- *   SR_OP_ANTIDIST_CLOSURE: 128, 256 or 512 (block width of the stream schedule) or
- *                           SR_TUNE_PERSISTENT (the persistent schedule);
+ *   SR_OP_ANTIDIST_CLOSURE: 128, 256 or 512 (block width of the stream schedule),
+ *                           SR_TUNE_PERSISTENT (the persistent schedule) or SR_TUNE_FUSED
+ *                           (one launch per pivot block, SR_OPT_CLOSURE_FUSED);
  *   SR_OP_BOOL_MUL:         SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES (Four Russians) or
  *                           SR_TUNE_BOOL_TENSOR;
  *   SR_OP_ANTIDIST_MUL:     128 or 64 (CTA tile side).
  * Choices are kept per (op, dtype, size bucket): buckets are 256, 384, 512, 768, 1024,
  * ... (powers of two and 1.5 times them) and a size uses the smallest bucket >= it. */
-enum { SR_TUNE_BOOL_WORDS = 0, SR_TUNE_BOOL_TABLES = 1, SR_TUNE_BOOL_TENSOR = 2, SR_TUNE_PERSISTENT = 1 };
+enum { SR_TUNE_BOOL_WORDS = 0, SR_TUNE_BOOL_TABLES = 1, SR_TUNE_BOOL_TENSOR = 2, SR_TUNE_PERSISTENT = 1,
+       SR_TUNE_FUSED = 2 };
 
 /* Time every schedule of the anti-distance closure (dtype u8/u16/u32) on a scratch
  * matrix of the bucket's order D' >= D (allocated and freed here; D' <= 65536) and record
  * the fastest for the bucket: stream schedules with blocks of 128, 256 and 512, and the
- * persistent schedule when the ctx workspace holds what it needs.  reps timed runs per
+ * persistent and fused-pass schedules (u8/u16) when the ctx workspace holds what they
+ * need.  reps timed runs per
  * candidate (best taken) after one untimed run, on `stream` (synchronised).  An existing
  * choice is returned without timing unless force != 0.  antidist_closure and
  * dist_closure then follow the choice while SR_OPT_CLOSURE_BLOCK is 0 and
- * SR_OPT_CLOSURE_PERSISTENT is 1 (their defaults).  Rewrites the ctx's tune cache.
+ * SR_OPT_CLOSURE_PERSISTENT and SR_OPT_CLOSURE_FUSED are 1 (their defaults).  Rewrites
+ * the ctx's tune cache.
  * Outputs (may be NULL): the choice and its time in ms. */
 sr_status sr_autotune_closure(sr_ctx *ctx, sr_dtype dtype, int64_t D, void *stream, int reps, int force,
                               int *choice, double *best_ms);

@@ -37,7 +37,8 @@ SR_OPT_CLOSURE_PERSISTENT = 5
 SR_OPT_CLOSURE_PANEL_SHARE = 6
 SR_OPT_BOOL_SIDE_SMS = 7
 SR_OPT_PRODUCT_SPLIT = 8
-SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES, SR_TUNE_BOOL_TENSOR, SR_TUNE_PERSISTENT = 0, 1, 2, 1
+SR_OPT_CLOSURE_FUSED = 9
+SR_TUNE_BOOL_WORDS, SR_TUNE_BOOL_TABLES, SR_TUNE_BOOL_TENSOR, SR_TUNE_PERSISTENT, SR_TUNE_FUSED = 0, 1, 2, 1, 2
 SR_OP_DIST_MUL = 4
 SR_EW_AND, SR_EW_OR, SR_EW_XOR, SR_EW_NOT = range(4)
 
@@ -221,7 +222,7 @@ def sr_closure_order(D: int, share: int = 128):
 
 
 def sr_autotune_closure(ctx, dtype: int, D: int, stream=None, reps: int = 2, force: bool = False):
-    """-> (choice, ms): block width 128/256/512 or SR_TUNE_PERSISTENT, and its time."""
+    """-> (choice, ms): block width 128/256/512, SR_TUNE_PERSISTENT or SR_TUNE_FUSED, and its time."""
     ch, ms = _int(), ctypes.c_double()
     _check(lib.sr_autotune_closure(ctx, dtype, D, _stream(stream), reps, 1 if force else 0, ctypes.byref(ch),
                                    ctypes.byref(ms)), "sr_autotune_closure")

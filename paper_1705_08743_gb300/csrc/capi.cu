@@ -247,6 +247,10 @@ sr_status sr_set_option(sr_ctx *c, int option, int value)
         c->bool_side_sms = value;
         return SR_OK;
     }
+    if (option == SR_OPT_CLOSURE_FUSED && value >= 0 && value <= 2) {
+        c->closure_fused = value;
+        return SR_OK;
+    }
     if (option == SR_OPT_PRODUCT_SPLIT && (value == 0 || value == 1)) {
         c->product_split = value;
         return SR_OK;
@@ -267,8 +271,8 @@ sr_status sr_workspace_query(int op, sr_dtype dtype, int64_t D, int method, size
     }
     if (op == SR_OP_BOOL_MUL && is_bool(dtype))
         *bytes = bool_tc_workspace(D, D, D);
-    if (op == SR_OP_ANTIDIST_CLOSURE && (dtype == SR_U8 || dtype == SR_U16))
-        *bytes = antidist_closure_persistent_workspace(D);                 // persistent schedule
+    if (op == SR_OP_ANTIDIST_CLOSURE && (dtype == SR_U8 || dtype == SR_U16))   // persistent / fused-pass schedules
+        *bytes = std::max(antidist_closure_persistent_workspace(D), closure_fused_workspace(D));
     if (op == SR_OP_DIST_MUL && is_anti(dtype))
         *bytes = (size_t)(2 * D * ((D + 15) / 16 * 16) * esize(dtype) + 1024);
     return SR_OK;
@@ -458,11 +462,33 @@ static int64_t persistent_min_d(sr_dtype t) { return t == SR_U8 ? kPersistentAut
 
 // The anti-distance closure of T in place: the persistent schedule where the context
 // allows it and holds its workspace, the stream schedules of closure.cu otherwise.
+// the fused-pass schedule, if this call can take it
+static bool fused_ok(const sr_ctx *c, int64_t D, sr_dtype dtype, bool vec)
+{
+    const size_t need = closure_fused_workspace(D);
+    return c && vec && (dtype == SR_U8 || dtype == SR_U16) && need > 0 && c->ws && c->ws_bytes >= need;
+}
+
+// D from which the fused-pass schedule is the automatic choice (u8, u16)
+static bool fused_auto(sr_dtype dtype, int64_t D)
+{
+    (void)dtype;
+    (void)D;
+    return false;
+}
+
 static sr_status closure_dispatch(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr_dtype dtype, bool vec,
                                   cudaStream_t s)
 {
-    int tuned = 0;      // a recorded choice applies while both options are automatic
-    if (c && c->closure_width == 0 && c->closure_persistent == 1 && tune_lookup(c, tune_key("closure", dtype, D), &tuned)) {
+    int tuned = 0;      // a recorded choice applies while the options are automatic
+    if (c && c->closure_width == 0 && c->closure_persistent == 1 && c->closure_fused == 1 &&
+        tune_lookup(c, tune_key("closure", dtype, D), &tuned)) {
+        if (tuned == SR_TUNE_FUSED) {
+            if (fused_ok(c, D, dtype, vec))
+                return launch_antidist_closure_fused(T, ldt, (int)D, dtype, c->ws, c->ws_bytes, c->d_status,
+                                                     c->spin_limit, s);
+            return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, 0);
+        }
         if (tuned != SR_TUNE_PERSISTENT)
             return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, tuned);
         const size_t need = antidist_closure_persistent_workspace(D);
@@ -471,6 +497,9 @@ static sr_status closure_dispatch(sr_ctx *c, void *T, int64_t ldt, int64_t D, sr
                                                       c->spin_limit, c->closure_share, s);
         return launch_antidist_closure(T, ldt, (int)D, dtype, vec, s, 0);
     }
+    if (c && c->closure_width == 0 && c->closure_fused > 0 && (c->closure_fused == 2 || fused_auto(dtype, D)) &&
+        fused_ok(c, D, dtype, vec))
+        return launch_antidist_closure_fused(T, ldt, (int)D, dtype, c->ws, c->ws_bytes, c->d_status, c->spin_limit, s);
     if (c && vec && c->closure_width == 0 && c->closure_persistent > 0 && (dtype == SR_U8 || dtype == SR_U16) &&
         (c->closure_persistent == 2 || D >= persistent_min_d(dtype))) {
         const size_t need = antidist_closure_persistent_workspace(D);

@@ -27,6 +27,7 @@ struct sr_ctx {
     int closure_persistent = 1;   // persistent closure: 0 never, 1 large D, 2 whenever possible
     int closure_share = 128;      // persistent closure: phase-3 share before the next panels (/256)
     int bool_side_sms = -1;       // Boolean tensor-core closure: SMs phase 3 leaves to the diagonal chain (-1: default)
+    int closure_fused = 1;        // fused-pass closure: 0 never, 1 automatic, 2 whenever possible
     int product_split = 1;        // deep u8/u16 products: last wave split along K in clusters (0 never, 1 auto)
     sr::ServeState *serve = nullptr;
     std::map<std::string, std::array<int, 3>> tune;   // autotuned batch configurations by signature

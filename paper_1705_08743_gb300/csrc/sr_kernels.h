@@ -70,6 +70,13 @@ constexpr int64_t kPersistentMaxD = 32768;
 // D from which the persistent schedule is the automatic choice; above kPersistentMaxD: never
 // (measured slower than the stream schedules at every size so far)
 constexpr int64_t kPersistentAutoMinU8 = kPersistentMaxD + 1, kPersistentAutoMinU16 = kPersistentMaxD + 1;
+// closure_fused.cu: u8/u16 closure with one launch per 128-wide pivot block (the next block's
+// phases 1-2 as work items of the current phase 3); device workspace for its counters
+// (0 if D is out of range), and the launch (16-byte aligned rows; status / spin_limit as for
+// the persistent schedule)
+size_t closure_fused_workspace(int64_t D);
+sr_status launch_antidist_closure_fused(void *T, int64_t ldt, int D, sr_dtype dt, void *ws, size_t ws_bytes,
+                                        int *status, int spin_limit, cudaStream_t s);
 size_t antidist_closure_persistent_workspace(int64_t D);   // 0: not available for this D
 sr_status launch_antidist_closure_persistent(void *T, int64_t ldt, int D, sr_dtype dt, void *ws, size_t ws_bytes,
                                              int *status, int spin_limit, int frac, cudaStream_t s);

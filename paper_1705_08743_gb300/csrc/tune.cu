@@ -276,6 +276,14 @@ sr_status sr_autotune_closure(sr_ctx *c, sr_dtype dtype, int64_t D, void *stream
         });
         if (ms >= 0) res.push_back({SR_TUNE_PERSISTENT, ms});
     }
+    const size_t need_f = closure_fused_workspace(Dt);
+    if (e == cudaSuccess && (dtype == SR_U8 || dtype == SR_U16) && need_f > 0 && c->ws && c->ws_bytes >= need_f) {
+        const double ms = time_candidate(c, s, std::max(1, reps), [&] {
+            return launch_antidist_closure_fused(T, ld, (int)Dt, dtype, c->ws, c->ws_bytes, c->d_status,
+                                                 c->spin_limit, s);
+        });
+        if (ms >= 0) res.push_back({SR_TUNE_FUSED, ms});
+    }
     cudaFree(T);
     if (e != cudaSuccess) return cuda_fail(e, "sr_autotune_closure: fill");
     if (res.empty())
@@ -391,7 +399,8 @@ sr_status sr_tune_set(sr_ctx *c, int op, sr_dtype dtype, int64_t D, int choice)
     const bool anti = dtype == SR_U8 || dtype == SR_U16 || dtype == SR_U32;
     const bool boolean = dtype == SR_BOOL_W32 || dtype == SR_BOOL_W64;
     const bool ok = (op == SR_OP_ANTIDIST_CLOSURE && anti &&
-                     (choice == 128 || choice == 256 || choice == 512 || choice == SR_TUNE_PERSISTENT)) ||
+                     (choice == 128 || choice == 256 || choice == 512 || choice == SR_TUNE_PERSISTENT ||
+                      (choice == SR_TUNE_FUSED && dtype != SR_U32))) ||
                     (op == SR_OP_BOOL_MUL && boolean && choice >= SR_TUNE_BOOL_WORDS && choice <= SR_TUNE_BOOL_TENSOR) ||
                     (op == SR_OP_ANTIDIST_MUL && anti && (choice == 128 || choice == 64));
     if (!ok || D <= 0)

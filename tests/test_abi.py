@@ -66,10 +66,10 @@ def test_workspace_query_without_device(lib):
     assert 2 * 16384 * 2048 < big < 4 * 16384 * 2048 + (64 << 20)     # phase 3's fp8 operands dominate
     sq = lib.sr_workspace_query(lib.SR_OP_BOOL_CLOSURE, lib.SR_BOOL_W64, 1000, lib.SR_CLOSURE_SQUARING)
     assert sq >= 2 * 1000 * 32 * 4
-    # the anti-distance closure's persistent schedule: a version per pivot-block pair, u8/u16 only,
-    # D in [128, 32768]
+    # the anti-distance closure's persistent schedule (a version per pivot-block pair, D in
+    # [128, 32768]) and fused-pass schedule (four counters per launch, D <= 32768): u8/u16 only
     pc = lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U8, 4096, 0)
     assert pc >= 4 * (4096 // 128) ** 2
     assert lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U32, 4096, 0) == 0
-    assert lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U8, 100, 0) == 0
+    assert lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U8, 100, 0) == 2 * 4 * 4   # two launches
     assert lib.sr_workspace_query(lib.SR_OP_ANTIDIST_CLOSURE, lib.SR_U16, 40000, 0) == 0
