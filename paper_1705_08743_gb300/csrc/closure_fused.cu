@@ -28,11 +28,10 @@
 // one's CTAs take the slots the current one's last CTAs leave and wait in hardware until
 // it has completed, so no launch gap separates the passes.
 //
-// GB300, u8 D = 4096: 2.59 ms against 2.65 ms for the stream schedule; slower at
-// D = 3584 (2.06 / 1.93 ms), 6144 (8.03 / 7.29) and u16 D = 4096 (4.80 / 4.73), where
-// the stream schedule's peer stream or a better-filled last wave wins.  Each launch is
-// bound by its 2.2 waves of 128-deep tiles (about 0.71 of the DPX peak).  The autotuner
-// times it beside the other schedules (SR_TUNE_FUSED).
+// GB300, against the stream schedule: u8 D = 4096 2.48 / 2.64 ms, u16 D = 4096 4.67 /
+// 4.73 ms; slower at u8 D = 2048 (1.22 / 0.82), 3584 (2.12 / 1.96) and 6144 (7.82 /
+// 7.29), where the stream schedule's peer stream or a better-filled last wave wins.  The
+// autotuner times it beside the other schedules (SR_TUNE_FUSED).
 
 #include <algorithm>
 
@@ -177,7 +176,10 @@ closure_fused_kernel(FusedArgs a)
         }
         return;
     }
-    if (it < f.n_strip) {                                 // 2. kb's update of row / column kb+1
+    // items 2, 4 and 5 share one call of the tile routine (one copy of its unrolled k-loop
+    // for the instruction cache); its loads go through L2, which item 5 needs
+    const bool strip = it < f.n_strip;
+    if (strip) {                                          // 2. kb's update of row / column kb+1
         if (it < f.tn) {
             p.A = T + (int64_t)f.k1 * ld + f.k0;
             p.B = T + (int64_t)f.k0 * ld;
@@ -192,44 +194,44 @@ closure_fused_kernel(FusedArgs a)
             p.R = a.D - f.ex; p.N = f.bwn; p.K = f.bw;
             p.rskip0 = f.k0; p.rskipw = f.ex;
         }
-        mul_tiles<KD, FB, FB, 32, 8, 16, VEC>(p, it, 1 << 30);
+    } else {
+        it -= f.n_strip + f.n_piv;
+        if (it < f.n_p3) {                                // 4. phase 3 of kb
+            p.A = T + f.k0;
+            p.B = T + (int64_t)f.k0 * ld;
+            p.C = T;
+            p.R = a.D - f.ex; p.N = a.D - f.ex; p.K = f.bw;
+            p.rskip0 = p.cskip0 = f.k0;
+            p.rskipw = p.cskipw = f.ex;
+        } else {
+            it -= f.n_p3;
+            if (it >= f.n_panel)
+                return;
+            // 5. phase 2 of kb+1, once block kb+1 is closed and the strips are done
+            if (!wait_counts(a, &a.ctr[1], 1, &a.ctr[2], f.n_strip))
+                return;
+            if (it < f.tp) {                              // row panel of kb+1, in place
+                p.A = T + (int64_t)f.k1 * ld + f.k1;
+                p.B = p.C = T + (int64_t)f.k1 * ld;
+                p.R = f.bwn; p.N = a.D - f.bwn; p.K = f.bwn;
+                p.cskip0 = f.k1; p.cskipw = f.bwn;
+            } else {                                      // column panel of kb+1, in place
+                it -= f.tp;
+                p.A = p.C = T + f.k1;
+                p.B = T + (int64_t)f.k1 * ld + f.k1;
+                p.R = a.D - f.bwn; p.N = f.bwn; p.K = f.bwn;
+                p.rskip0 = f.k1; p.rskipw = f.bwn;
+            }
+        }
+    }
+    mul_tiles<KD, FB, FB, 32, 8, 16, VEC, true>(p, it, 1 << 30);
+    if (strip) {
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&a.ctr[2], 1);
         }
-        return;
     }
-    it -= f.n_strip + f.n_piv;
-    if (it < f.n_p3) {                                    // 3. phase 3 of kb
-        p.A = T + f.k0;
-        p.B = T + (int64_t)f.k0 * ld;
-        p.C = T;
-        p.R = a.D - f.ex; p.N = a.D - f.ex; p.K = f.bw;
-        p.rskip0 = p.cskip0 = f.k0;
-        p.rskipw = p.cskipw = f.ex;
-        mul_tiles<KD, FB, FB, 32, 8, 16, VEC>(p, it, 1 << 30);
-        return;
-    }
-    it -= f.n_p3;
-    if (it >= f.n_panel)
-        return;
-    // 4. phase 2 of kb+1, once phase 1 of kb+1 and the strips are done
-    if (!wait_counts(a, &a.ctr[1], 1, &a.ctr[2], f.n_strip))
-        return;
-    if (it < f.tp) {                                      // row panel of kb+1, in place
-        p.A = T + (int64_t)f.k1 * ld + f.k1;
-        p.B = p.C = T + (int64_t)f.k1 * ld;
-        p.R = f.bwn; p.N = a.D - f.bwn; p.K = f.bwn;
-        p.cskip0 = f.k1; p.cskipw = f.bwn;
-    } else {                                              // column panel of kb+1, in place
-        it -= f.tp;
-        p.A = p.C = T + f.k1;
-        p.B = T + (int64_t)f.k1 * ld + f.k1;
-        p.R = a.D - f.bwn; p.N = f.bwn; p.K = f.bwn;
-        p.rskip0 = f.k1; p.rskipw = f.bwn;
-    }
-    mul_tiles<KD, FB, FB, 32, 8, 16, VEC, true>(p, it, 1 << 30);   // operands written in this launch: via L2
 }
 
 template <class KD>
