@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched (config 4) summary")
     ap.add_argument("--no-bool", action="store_true",
                     help="default workload: skip the Boolean closure (config 3, D=16384) summary")
-    ap.add_argument("--closure", default="auto", choices=["auto", "persistent", "stream"],
+    ap.add_argument("--closure", default="auto", choices=["auto", "persistent", "fused", "stream"],
                     help="anti-distance closure schedule (auto: the library's choice with the workspace it asks for)")
     ap.add_argument("--tuning", default="", help="batched workloads: cluster,threshold,ctas_per_sm (skips autotune)")
     ap.add_argument("--only", default="", choices=["", "mul", "closure"],
@@ -142,14 +142,16 @@ CLOSURE_TUNED = {}
 
 
 def closure_ctx(D, sdt, mode="auto"):
-    """A context for the anti-distance closure: its workspace holds what the persistent
-    schedule needs (sr_workspace_query).  mode "auto": the library's autotuner times
-    every schedule at this size (stream blocks of 128/256/512, persistent) before any
-    timed step and the closure follows its choice; "persistent" / "stream" force one."""
+    """A context for the anti-distance closure: its workspace holds what the persistent and
+    fused-pass schedules need (sr_workspace_query).  mode "auto": the library's autotuner
+    times every schedule at this size (stream blocks of 128/256/512, persistent, fused
+    passes) before any timed step and the closure follows its choice; "persistent" /
+    "fused" / "stream" force one."""
     import paper_1705_08743_gb300 as sr
     ws = sr.sr_workspace_query(sr.SR_OP_ANTIDIST_CLOSURE, sdt, D) if sdt in (sr.SR_U8, sr.SR_U16) else 0
     ctx = sr.sr_create(workspace_bytes=ws)
-    sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_PERSISTENT, {"auto": 1, "persistent": 2, "stream": 0}[mode])
+    sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_PERSISTENT, {"auto": 1, "persistent": 2, "fused": 0, "stream": 0}[mode])
+    sr.sr_set_option(ctx, sr.SR_OPT_CLOSURE_FUSED, {"auto": 1, "persistent": 0, "fused": 2, "stream": 0}[mode])
     if mode == "auto":
         choice, ms = sr.sr_autotune_closure(ctx, sdt, D, reps=2)
         name = {sr.SR_TUNE_PERSISTENT: "persistent", sr.SR_TUNE_FUSED: "fused passes (one launch per pivot block)"}
