@@ -318,9 +318,10 @@ __device__ __forceinline__ void expand_word(uint32_t bits, uint8_t *dst)
     uint32_t o[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        // bit j of the nibble to bit 8j (the multiply's four copies shifted by 0, 7, 14, 21
+        // put bit j at 8j, and the mask drops the rest), then each 0x01 byte to e4m3 1.0
         const uint32_t nib = (bits >> (4 * q)) & 0xFu;
-        o[q] = ((nib & 1u) ? 0x38u : 0u) | ((nib & 2u) ? 0x3800u : 0u) | ((nib & 4u) ? 0x380000u : 0u) |
-               ((nib & 8u) ? 0x38000000u : 0u);
+        o[q] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
     }
     uint4 *d = reinterpret_cast<uint4 *>(dst);
     d[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -341,6 +342,22 @@ __device__ __forceinline__ void expand_rows_items(const uint32_t *M, int64_t ldm
     }
 }
 
+// 32 x 32 bit transpose across a warp: lane i holds row i (bit j = column j) and gets
+// column i (bit j = row j).  Five stages swap the off-diagonal halves of ever smaller
+// blocks (16, 8, 4, 2, 1 bits) with the lane s apart, masks selecting the half kept.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int s = 16 >> st;
+        const uint32_t m = st == 0 ? 0x0000FFFFu : st == 1 ? 0x00FF00FFu : st == 2 ? 0x0F0F0F0Fu
+                         : st == 3 ? 0x33333333u : 0x55555555u;
+        const uint32_t p = __shfl_xor_sync(0xFFFFFFFFu, x, s);
+        x = (lane & s) ? (x & ~m) | ((p >> s) & m) : (x & m) | ((p & m) << s);
+    }
+    return x;
+}
+
 // transpose + expand: out[n][k] = bit (k, n) of M (K rows of bits), rows n < N, zero past K;
 // item t (one warp) transposes the 32 x 32 bits of word w of rows 32kb .. 32kb + 31
 __device__ __forceinline__ void expand_cols_items(const uint32_t *M, int64_t ldm, int K, int N, uint8_t *out, int Kp,
@@ -353,12 +370,7 @@ __device__ __forceinline__ void expand_cols_items(const uint32_t *M, int64_t ldm
         const int w = (int)(t / kblocks), kb = (int)(t % kblocks);
         const int k = 32 * kb + lane;
         const uint32_t word = k < K ? M[(int64_t)k * ldm + w] : 0u;   // row k, columns 32w .. 32w+31
-        uint32_t mine = 0u;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t b = __ballot_sync(0xFFFFFFFFu, (word >> j) & 1u);   // column 32w + j, rows 32kb..+31
-            if (lane == j) mine = b;
-        }
+        const uint32_t mine = warp_transpose32(word, lane);           // column 32w + lane, rows 32kb..+31
         const int n = 32 * w + lane;
         if (n < N) expand_word(mine, out + (int64_t)n * Kp + 32 * kb);
     }
