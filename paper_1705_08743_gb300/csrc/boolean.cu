@@ -18,6 +18,7 @@
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace sr {
 
@@ -546,6 +547,7 @@ static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, b
     cudaStream_t sp = side_stream(0), sr_ = side_stream(1), sc = side_stream(2);
     if (!sp || !sr_ || !sc) {   // single stream: phase 2, phase 3, next pivot
         for (int kb = 0; kb < nb; ++kb) {
+            SR_TRACE_BLOCK("bool_closure.block", kb);
             const int k0 = kb * PB, bw = width(kb), kw = k0 / 32, wn = word_end(kb, 1) - kw;
             SR_TRY(launch_bool_mul(row_panel(kb), vec, s, 2));
             SR_TRY(launch_bool_mul(col_panel(kb), vec, s, 1));
@@ -567,6 +569,7 @@ static sr_status bool_closure_blocked(uint32_t *T, int64_t ldt, int D, int rw, b
     SR_CUDA_CHECK(cudaEventRecord(rowp_done[0], s));
     SR_CUDA_CHECK(cudaEventRecord(colp_done[0], s));
     for (int kb = 0; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("bool_closure.block", kb);
         const int k0 = kb * PB, bw = width(kb), kw = k0 / 32;
         const bool next = kb + 1 < nb;
         const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;          // rows left out
@@ -764,6 +767,7 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void
     cudaEvent_t *colp_start = diag_done + nb + 1, *colp_done = colp_start + nb + 1;
     SR_TRY(close_block(0, s));
     for (int kb = 0; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("bool_closure.block", kb);
         const int k0 = kb * W, bw = width(kb), kw = k0 / 32, wn = words_of(kb);
         const bool next = kb + 1 < nb;
         SR_CUDA_CHECK(cudaEventRecord(colp_start[kb], s));

@@ -21,6 +21,7 @@
 
 #include "sr_common.cuh"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace sr {
 
@@ -131,6 +132,7 @@ sr_status closure_one_stream(void *T, int64_t ldt, int D, bool vec, sr_dtype dt,
     const int nb = (D + PB - 1) / PB;
     SR_TRY(launch_antidist_pivot(T, ldt, D, 0, -1, dt, vec, s));
     for (int kb = 0; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("antidist_closure.block", kb);
         const int k0 = kb * PB, bw = std::min(PB, D - k0);
         SR_TRY(phase2<E>(T, ldt, D, k0, bw, true, dt, vec, s));
         SR_TRY(phase2<E>(T, ldt, D, k0, bw, false, dt, vec, s));
@@ -173,6 +175,7 @@ sr_status closure_two_streams(void *T, int64_t ldt, int D, bool vec, sr_dtype dt
     SR_TRY(event_pool(4 * (size_t)nb + 4, ev));
     SR_TRY(launch_antidist_pivot(T, ldt, D, 0, -1, dt, vec, s));
     for (int kb = 0; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("antidist_closure.block", kb);
         const int k0 = kb * PB, bw = std::min(PB, D - k0);
         const bool next = kb + 1 < nb;
         cudaEvent_t *e = ev->data() + 4 * kb;
@@ -274,6 +277,7 @@ sr_status closure_look_ahead(void *T, int64_t ldt, int D, int W, bool vec, sr_dt
     SR_CUDA_CHECK(cudaEventRecord(rowp_done[0], s));
     SR_CUDA_CHECK(cudaEventRecord(colp_done[0], s));
     for (int kb = 0; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("antidist_closure.block", kb);
         const int k0 = kb * W, bw = width(kb);
         const bool next = kb + 1 < nb;
         const int bwn = next ? width(kb + 1) : 0, ex = bw + bwn;     // rows/columns left out

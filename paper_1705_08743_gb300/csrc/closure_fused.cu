@@ -39,6 +39,7 @@
 #include "diag128.cuh"
 #include "sr_common.cuh"
 #include "sr_kernels.h"
+#include "sr_trace.h"
 
 namespace sr {
 namespace {
@@ -254,6 +255,7 @@ sr_status launch_fused(void *T, int64_t ldt, int D, void *ws, size_t ws_bytes, i
     int *ctr = static_cast<int *>(ws);
     SR_CUDA_CHECK(cudaMemsetAsync(ctr, 0, need, s));
     for (int kb = -1; kb < nb; ++kb) {
+        SR_TRACE_BLOCK("antidist_closure.block", kb);
         const FusedShape f(D, nb, kb);
         const int n = f.items();
         if (n <= 0)

@@ -31,7 +31,14 @@ static nvtxDomainHandle_t NVTX_API rec_domain_create(const char *name)
 
 static int NVTX_API rec_push(nvtxDomainHandle_t d, const nvtxEventAttributes_t *a)
 {
-    append("push", d, (a && a->messageType == NVTX_MESSAGE_TYPE_ASCII) ? a->message.ascii : "");
+    const char *name = (a && a->messageType == NVTX_MESSAGE_TYPE_ASCII) ? a->message.ascii : "";
+    if (a && a->payloadType == NVTX_PAYLOAD_TYPE_INT64) {      /* name#payload */
+        char buf[96];
+        snprintf(buf, sizeof buf, "%s#%lld", name, (long long)a->payload.llValue);
+        append("push", d, buf);
+    } else {
+        append("push", d, name);
+    }
     return 0;
 }
 
