@@ -58,7 +58,9 @@ antidist_mul_grouped_kernel(const MulArgs *args, const int *start, int n)
         else hi = mid - 1;
     }
     const MulArgs p = args[lo];
-    mul_tiles<KD, BM, BN, BK, TM, TN, VEC>(p, b - start[lo], 1 << 30);
+    // many small products: their ragged edge tiles skip the empty half (128-wide tiles)
+    constexpr bool kRagged = TM % 8 == 0 && (TN / 2) % 8 == 0;
+    mul_tiles<KD, BM, BN, BK, TM, TN, VEC, false, 0, false, kRagged>(p, b - start[lo], 1 << 30);
 }
 
 // -------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 // (closure_persistent.cu).  See antidist.cu for the method.
 #pragma once
 
+#include <type_traits>
+
 #include "sr_common.cuh"
 #include "sr_kernels.h"
 
@@ -147,8 +149,13 @@ __device__ __forceinline__ void cluster_max8(uint32_t (&x)[8], uint32_t a, uint3
 // back, taking the lanewise max with the other ranks' through distributed shared memory
 // (⊕ = max is associative and commutative, so the slices may merge in any order), and
 // alone runs the epilogue.  One tile per CTA, no skipped tiles.
+//
+// RAGGED: a tile whose valid rows (columns) all lie in its first half skips the other
+// half's accumulators in the k-loop (their entries are never stored), so a ragged edge
+// tile costs about what a half-size tile would.  The choice is uniform across the CTA and
+// made once per k-panel among four copies of the k-loop.
 template <class KD, int BM, int BN, int BK, int TM, int TN, bool VEC, bool CG = false, int SYNC = 0,
-          bool SPLIT = false>
+          bool SPLIT = false, bool RAGGED = false>
 __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int stride, int tile_end = 0x7fffffff,
                                           int kslice = 0)
 {
@@ -329,30 +336,48 @@ __device__ __forceinline__ void mul_tiles(const MulArgs &p, int tile0, int strid
             const uint32_t *a0p = sA0 + buf * BK * BM + tr * 4;
             const uint32_t *a1p = sA1 + buf * BK * BM + tr * 4;
             const uint32_t *bp = sB + buf * BK * BN2 + tc * 4;
+            // thread rows i < TM/2 are the tile's first BM/2 rows (accumulator group g = i / 4
+            // holds rows g·4·TR + tr·4 + i % 4), lane pairs j < NP/2 its first BN/2 columns
+            auto kpanel = [&](auto half_r, auto half_c) {
+                constexpr int TMA = decltype(half_r)::value ? TM / 2 : TM;
+                constexpr int NPA = decltype(half_c)::value ? NP / 2 : NP;
 #pragma unroll 4
-            for (int k = 0; k < BK; ++k) {
-                uint32_t a0[TM], a1[TM], b[NP];
+                for (int k = 0; k < BK; ++k) {
+                    uint32_t a0[TM], a1[TM], b[NP];
 #pragma unroll
-                for (int g = 0; g < TM / 4; ++g) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(a0p + k * BM + g * 4 * TR);
-                    a0[4 * g] = v.x; a0[4 * g + 1] = v.y; a0[4 * g + 2] = v.z; a0[4 * g + 3] = v.w;
-                    if (KD::AW == 2) {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(a1p + k * BM + g * 4 * TR);
-                        a1[4 * g] = w.x; a1[4 * g + 1] = w.y; a1[4 * g + 2] = w.z; a1[4 * g + 3] = w.w;
-                    } else {
-                        a1[4 * g] = a1[4 * g + 1] = a1[4 * g + 2] = a1[4 * g + 3] = 0u;
+                    for (int g = 0; g < TMA / 4; ++g) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(a0p + k * BM + g * 4 * TR);
+                        a0[4 * g] = v.x; a0[4 * g + 1] = v.y; a0[4 * g + 2] = v.z; a0[4 * g + 3] = v.w;
+                        if (KD::AW == 2) {
+                            const uint4 w = *reinterpret_cast<const uint4 *>(a1p + k * BM + g * 4 * TR);
+                            a1[4 * g] = w.x; a1[4 * g + 1] = w.y; a1[4 * g + 2] = w.z; a1[4 * g + 3] = w.w;
+                        } else {
+                            a1[4 * g] = a1[4 * g + 1] = a1[4 * g + 2] = a1[4 * g + 3] = 0u;
+                        }
                     }
+#pragma unroll
+                    for (int g = 0; g < NPA / 4; ++g) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(bp + k * BN2 + g * 4 * TC);
+                        b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < TMA; ++i)
+#pragma unroll
+                        for (int j = 0; j < NPA; ++j)
+                            acc[i][j] = KD::op(acc[i][j], b[j], a0[i], a1[i]);
                 }
-#pragma unroll
-                for (int g = 0; g < NP / 4; ++g) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(bp + k * BN2 + g * 4 * TC);
-                    b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
-                }
-#pragma unroll
-                for (int i = 0; i < TM; ++i)
-#pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        acc[i][j] = KD::op(acc[i][j], b[j], a0[i], a1[i]);
+            };
+            using F = std::false_type;
+            using Tr = std::true_type;
+            if constexpr (RAGGED) {
+                static_assert(TM % 8 == 0 && NP % 8 == 0, "halves of whole accumulator groups");
+                const bool hr = p.R - row0 <= BM / 2, hc = p.N - col0 <= BN / 2;
+                if (hr && hc) kpanel(Tr{}, Tr{});
+                else if (hr) kpanel(Tr{}, F{});
+                else if (hc) kpanel(F{}, Tr{});
+                else kpanel(F{}, F{});
+            } else {
+                kpanel(F{}, F{});
             }
             if (kt + 1 < nkt)
                 sstore(buf ^ 1);
