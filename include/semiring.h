@@ -158,6 +158,17 @@ typedef enum {
 } sr_option;
 sr_status sr_set_option(sr_ctx *ctx, int option, int value);
 
+/* ---------------------------------------------------------------- host buffers */
+
+/* *mapped := 1 if p is pinned host memory (cudaHostAlloc / cudaHostRegister, e.g. a
+ * torch pin_memory() tensor) that the current device addresses at the same pointer
+ * (unified addressing), else 0 (device memory, pageable or unknown host memory).  Such
+ * buffers may be passed as operands, or as the output of a call that never reads it
+ * (accumulate = 0): the kernels then read and write host memory over the host link
+ * (NVLink-C2C on Grace), with no staging copy.  Pass nothing else that is not device
+ * memory.  Errors: SR_EINVAL for a NULL mapped. */
+sr_status sr_host_mapped(const void *p, int *mapped);
+
 /* ---------------------------------------------------------------- row-sharded products */
 
 /* Rows [*r0, *r1) of an R-row product for `rank` of `world` processes (one GPU each).

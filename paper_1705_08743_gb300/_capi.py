@@ -111,6 +111,7 @@ _SIGS = {
     "bool_closure_squaring_noalloc": (_st, [_vp, _i64, _i64, _int, _vp]),
     "sr_closure_order": (ctypes.c_longlong, [_i64, _int, _vp, ctypes.c_longlong]),
     "sr_shard_rows": (_st, [_i64, _int, _int, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "sr_host_mapped": (_st, [_vp, ctypes.POINTER(_int)]),
     "sr_autotune_closure": (_st, [_vp, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
                                   ctypes.POINTER(ctypes.c_double)]),
     "sr_autotune_mul": (_st, [_vp, _int, _int, _i64, _vp, _int, _int, ctypes.POINTER(_int),
@@ -256,6 +257,15 @@ def sr_tune_save(ctx, path: str):
 
 def sr_tune_load(ctx, path: str):
     _check(lib.sr_tune_load(ctx, path.encode()), "sr_tune_load")
+
+
+def sr_host_mapped(p) -> bool:
+    """Whether p (a pointer, or a tensor's data_ptr()) is pinned host memory the current
+    device addresses at the same pointer."""
+    m = _int()
+    ptr = p.data_ptr() if hasattr(p, "data_ptr") else p
+    _check(lib.sr_host_mapped(ptr, ctypes.byref(m)), "sr_host_mapped")
+    return bool(m.value)
 
 
 def sr_shard_rows(R: int, world: int, rank: int, align: int = 128):

@@ -138,6 +138,24 @@ extern "C" {
 
 const char *sr_last_error(void) { return g_err.c_str(); }
 
+sr_status sr_host_mapped(const void *p, int *mapped)
+{
+    SR_TRACE("sr_host_mapped");
+    if (!mapped)
+        return fail(SR_EINVAL, "sr_host_mapped: mapped is NULL");
+    *mapped = 0;
+    if (!p)
+        return SR_OK;
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();                 // unregistered host memory: not mapped
+        return SR_OK;
+    }
+    *mapped = a.type == cudaMemoryTypeHost && a.devicePointer == p ? 1 : 0;
+    return SR_OK;
+}
+
 sr_status sr_shard_rows(int64_t R, int world, int rank, int64_t align, int64_t *r0, int64_t *r1)
 {
     if (!r0 || !r1 || R < 0 || world < 1 || rank < 0 || rank >= world || align < 1)
