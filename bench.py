@@ -743,7 +743,8 @@ class CfgBool:
                                                                            sr.SR_CLOSURE_WARSHALL))
         self.mul_events = []
 
-    def step(self, stream, record_mul=False):
+    def step(self, stream, record_mul=False, dense=None):
+        """dense: where config 3 packs its input from (default: the device copy)."""
         import torch
         sr, D, s = self.sr, self.D, stream.cuda_stream
         if record_mul:
@@ -754,7 +755,7 @@ class CfgBool:
         elif self.kind == "prod16k":
             sr.bool_mul(self.ctx, self.A, self.nw, self.B, self.nw, self.T, self.nw, D, D, D, self.dt, 0, s)
         else:
-            sr.bool_pack(None, self.dense, D, self.T, self.nw, D, D, self.dt, s)
+            sr.bool_pack(None, self.dense if dense is None else dense, D, self.T, self.nw, D, D, self.dt, s)
             sr.bool_closure(self.wctx, self.T, self.nw, D, self.dt, sr.SR_CLOSURE_WARSHALL, s)
         if record_mul:
             e1.record(stream)
@@ -817,17 +818,29 @@ class CfgBool:
         if self.kind == "cfg1":
             self.hB = torch.from_numpy(B).pin_memory()
             self.h2d *= 2
+        # the pack kernels read the dense 0/1 input in pinned host memory where the device maps it
+        sr = self.sr
+        self.zero_copy = sr.sr_host_mapped(self.hA) and (self.kind != "cfg1" or sr.sr_host_mapped(self.hB))
+        self.transfer = ("zero-copy: the pack kernels read the dense input in pinned host memory over the host "
+                         "link; the result copied back" if self.zero_copy else
+                         "copies: the dense input uploaded, the result copied back")
 
     def e2e_step(self, stream):
         sr, D, s = self.sr, self.D, stream.cuda_stream
-        self.dense.copy_(self.hA, non_blocking=True)
+        if self.zero_copy:
+            src_a, src_b = self.hA, getattr(self, "hB", None)
+        else:
+            self.dense.copy_(self.hA, non_blocking=True)
+            src_a = self.dense
+            if self.kind == "cfg1":
+                self.denseB.copy_(self.hB, non_blocking=True)
+                src_b = self.denseB
         if self.kind == "cfg1":
-            self.denseB.copy_(self.hB, non_blocking=True)
-            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt, s)
-            sr.bool_pack(None, self.denseB, D, self.B, self.nw, D, D, self.dt, s)
+            sr.bool_pack(None, src_a, D, self.A, self.nw, D, D, self.dt, s)
+            sr.bool_pack(None, src_b, D, self.B, self.nw, D, D, self.dt, s)
         elif self.kind == "prod16k":
-            sr.bool_pack(None, self.dense, D, self.A, self.nw, D, D, self.dt, s)
-        self.step(stream)
+            sr.bool_pack(None, src_a, D, self.A, self.nw, D, D, self.dt, s)
+        self.step(stream, dense=src_a)
         self.hT.copy_(self.T, non_blocking=True)
 
     def cpu_sample(self, A, B):

@@ -55,3 +55,24 @@ def test_encode_and_product_on_pinned_host_buffers(D):
     sr.antidist_mul(None, torch.from_numpy(A).cuda(), D, Bd, D, Cd, D, D, D, D, sr.SR_U8, 0)
     torch.cuda.synchronize()
     assert np.array_equal(Cd.cpu().numpy(), hC.numpy())
+
+
+def test_pack_from_pinned_host_input():
+    """bool_pack reads a dense 0/1 matrix in pinned host memory (the Boolean workloads'
+    zero-copy input path): the same words as packing the device copy, and the oracle's
+    bit layout (Section 4 matBool)."""
+    import torch
+    import paper_1705_08743_gb300 as sr
+    D = 1000
+    dense = synth.bool_dag_union(D, seed=7).astype(np.uint8)
+    h = torch.from_numpy(dense).pin_memory()
+    if not sr.sr_host_mapped(h):
+        pytest.skip("pinned host memory is not mapped into the device address space")
+    nw = (D + 31) // 32
+    out_h = torch.zeros((D, nw), dtype=torch.int32, device="cuda")
+    out_d = torch.zeros_like(out_h)
+    sr.bool_pack(None, h, D, out_h, nw, D, D, sr.SR_BOOL_W32)
+    sr.bool_pack(None, torch.from_numpy(dense).cuda(), D, out_d, nw, D, D, sr.SR_BOOL_W32)
+    torch.cuda.synchronize()
+    assert torch.equal(out_h, out_d)
+    assert np.array_equal(out_h.cpu().numpy().view(np.uint32), oracle.pack_bits(dense).view(np.uint32))
