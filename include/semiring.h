@@ -12,7 +12,8 @@
  *                                 for distance d, 0 for "no path / distance >= S".
  *
  * Conventions shared by every call
- *  - Pointers to matrix data are DEVICE pointers owned by the caller; the
+ *  - Pointers to matrix data are DEVICE pointers owned by the caller (or pinned
+ *    host memory the device maps at the same pointer: sr_host_mapped); the
  *    library never frees them.  Matrices are row-major with a leading
  *    dimension ld >= row width, in elements (u8/u16/u32) or in words of the
  *    Boolean word type (32- or 64-bit).
