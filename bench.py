@@ -975,7 +975,8 @@ def run_ours(args, world, rank, local):
         return
     wl.only = args.only
     if hasattr(wl, "closure_mode"):
-        wl.closure_mode = args.closure
+        # a product-only run needs no closure autotune (its launches would come first)
+        wl.closure_mode = "stream" if args.only == "mul" and args.closure == "auto" else args.closure
     if args.tuning:
         wl.fixed_tuning = tuple(int(x) for x in args.tuning.split(","))
     WA, WB = wl.host_inputs()
