@@ -187,6 +187,10 @@ def sha_of(paths):
     return h.hexdigest()[:16]
 
 
+FUSED_SOURCES = ["paper_1705_08743_gb300/csrc/closure_fused.cu", "paper_1705_08743_gb300/csrc/antidist_tile.cuh",
+                 "paper_1705_08743_gb300/csrc/diag128.cuh", "paper_1705_08743_gb300/csrc/sr_common.cuh"]
+
+
 def load_traffic(kernel_key: str, sources, workload: str):
     """DRAM bytes per launch from a committed ncu capture of this workload's launch, if the
     kernel is unchanged since (traffic does not scale with the op count, so a capture at
@@ -1125,13 +1129,31 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     nl = sr.sr_kernel_launches() - n0
     nb = (wl.D + 127) // 128
+    fused = nl == nb + 1 and nl != 1
+    fused_key = f"closure_fused_kernel<Kind{wl.dtype.upper()}>"
     kernel = ("antidist_closure stream schedule (pivot-block kernel, panel and phase-3 products)" if nl not in (1, nb + 1)
               else f"antidist_closure_persistent_kernel<Kind{wl.dtype.upper()}> (whole closure, one launch)" if nl == 1
-              else f"closure_fused_kernel<Kind{wl.dtype.upper()}> (one launch per pivot block)")
+              else f"{fused_key} (one launch per pivot block)")
+    # one closure: nl launches on one stream; per launch D^3 / nl ops in clo_avg / nl ms
     roof_closure = {"bound": "alu", "kernel": kernel,
                     "achieved": clo_achieved, "peak": peak, "unit": "Gop/s", "frac": clo_achieved / peak,
-                    "launch_ms": clo_avg, "timing": "CUDA events around the antidist_closure call, encode excluded",
+                    "launch_ms": clo_avg / nl, "launches_per_closure": nl, "closure_ms": clo_avg,
+                    "timing": "CUDA events around the antidist_closure call, encode excluded",
+                    "traffic": load_traffic(fused_key, FUSED_SOURCES, args.workload) if fused else None,
                     "schedule": CLOSURE_TUNED.get(wl.D, "forced by --closure")}
+    roof_product = {"bound": "alu", "kernel": wl.roofline_kernel, "achieved": achieved, "peak": peak,
+                    "unit": "Gop/s", "frac": achieved / peak,
+                    "peak_source": "measured now: issue-bound DPX add-max stream on all SMs (sr_peak_probe)",
+                    "launch_ms": mul_avg,
+                    "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload)}
+    # the dominant kernel by live time in the step: the product kernel, which the stream
+    # schedule's phase 3 also runs, unless the closure is one kernel that takes longer
+    if fused and clo_avg > mul_avg:
+        roofline = dict(roof_closure, peak_source=roof_product["peak_source"], product=roof_product,
+                        dominant="the closure's kernel: the larger share of the step's CUDA-event time")
+    else:
+        roofline = dict(roof_product, closure=roof_closure,
+                        dominant="the product kernel (also the stream schedule's phase 3)")
     extra = {}
     if wl.D == 4096 and wl.dtype == "u8" and not args.no_8192:
         extra["closure_8192"] = closure_8192(dev, stream, flush, peak, local, args)
@@ -1146,12 +1168,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": wl.name, "step": "encode x3 + closure (in place) + product",
                    "ops_per_step": wl.ops, "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": wl.roofline_kernel, "achieved": achieved, "peak": peak,
-                     "unit": "Gop/s", "frac": achieved / peak,
-                     "peak_source": "measured now: issue-bound DPX add-max stream on all SMs (sr_peak_probe)",
-                     "launch_ms": mul_avg,
-                     "traffic": load_traffic(wl.roofline_kernel, wl.roofline_sources, args.workload),
-                     "closure": roof_closure},
+        "roofline": roofline,
         "parts_ms": {"product": mul_avg, "closure": clo_avg, "encode_x3": ms_per_step - mul_avg - clo_avg},
         "extra": extra,
         "cpu_baseline": cpu,
