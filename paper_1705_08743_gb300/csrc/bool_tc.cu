@@ -602,12 +602,13 @@ uint8_t *tc_operand_b(uint8_t *Ae, int64_t R, int Kp)
 }
 
 sr_status launch_square_prep(const uint32_t *M, const uint32_t *M2, int64_t ld, int D, int rw, void *ws, int *flags,
-                             int it, cudaStream_t s)
+                             int it, cudaStream_t s, int grid_sms)
 {
     const int Kp = (D + tc::BK - 1) / tc::BK * tc::BK;
     uint8_t *Ae = static_cast<uint8_t *>(ws);
     uint8_t *Be = tc_operand_b(Ae, D, Kp);
-    const int sms = device_sm_count();
+    // its loops stride over the grid, so any grid size gives the same result
+    const int sms = grid_sms > 0 ? std::min(grid_sms, device_sm_count()) : device_sm_count();
     const int64_t ncmp = (int64_t)D * rw, nrows = (int64_t)D * (Kp / 32), ncols = (int64_t)((D + 31) / 32) * (Kp / 32);
     const int nb_cmp = (int)std::max<int64_t>(1, std::min<int64_t>((ncmp + 255) / 256, sms * 4));
     const int nb_rows = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + 255) / 256, sms * 8));

@@ -645,7 +645,7 @@ size_t bool_squaring_workspace(int64_t D, int64_t rw)
 }
 
 sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes, bool tc,
-                                       int *status, int spin_limit, cudaStream_t s)
+                                       int *status, int spin_limit, cudaStream_t s, int grid_sms)
 {
     // flags (256 bytes), then M, M2: D rows of rw 32-bit words each, rows padded to a
     // multiple of 4 words; any workspace beyond them holds the tensor-core operands when
@@ -682,7 +682,7 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
         if (tcpath) {
             // one launch tests whether squaring it-1 changed M and expands M for this product,
             // which runs only if it did (flag it mod 3); two launches a squaring instead of four
-            SR_TRY(launch_square_prep(M, M2, ldw, D, rw, tcws, flags, it, s));
+            SR_TRY(launch_square_prep(M, M2, ldw, D, rw, tcws, flags, it, s, grid_sms));
             BoolArgs a = bool_args(M, M, M2, ldw, D, D, D, rw);
             a.accumulate = 0;
             const int Kp = (D + 127) / 128 * 128;
@@ -752,10 +752,14 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void
     void *ws_col = static_cast<char *>(ws) + half;
     void *ws_side = static_cast<char *>(ws) + main_bytes;
     const size_t side_bytes = ws_bytes - main_bytes;
+    // the diagonal blocks after block 0 close beside phase 3: their convergence tests and
+    // operand expansions take a grid sized for half the side SMs (GB300, D = 16384: 4.54 ms
+    // against 4.68 with a grid for every SM, whose blocks slowed phase 3 down)
     auto close_block = [&](int kb, cudaStream_t st) {
         const int k0 = kb * W;
         return launch_bool_closure_squaring(T + (int64_t)k0 * ldt + k0 / 32, ldt, width(kb), words_of(kb), ws_side,
-                                            side_bytes, true, status, spin_limit, st);
+                                            side_bytes, true, status, spin_limit, st,
+                                            kb > 0 && side_sms > 1 ? side_sms / 2 : 0);
     };
     SR_TRY(bool_clear_pad(T, ldt, D, rw, s));
     cudaStream_t sp = side_stream(0), sc = side_stream(1);

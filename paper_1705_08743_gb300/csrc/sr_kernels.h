@@ -137,8 +137,9 @@ uint8_t *tc_operand_b(uint8_t *Ae, int64_t R, int Kp);   // where B^T follows A 
 // (did squaring it - 1 change M: M != M2; it = 0: 1), clears flags[(it + 1) % 3], and
 // expands M into both operands of M ⊗ M at ws (layout of launch_bool_mul_tc's workspace);
 // after a squaring that changed nothing the flag stays 0 and nothing is expanded.
+// (grid_sms > 0: a grid sized for that many SMs, for a chain that runs beside other work)
 sr_status launch_square_prep(const uint32_t *M, const uint32_t *M2, int64_t ld, int D, int rw, void *ws, int *flags,
-                             int it, cudaStream_t s);
+                             int it, cudaStream_t s, int grid_sms = 0);
 // Four Russians (bool_m4r.cu); excluded ranges as in launch_bool_mul, no split K
 sr_status launch_bool_mul_m4r(const BoolArgs &a, cudaStream_t s);
 sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, bool vec, cudaStream_t s);
@@ -146,7 +147,7 @@ sr_status launch_bool_closure_warshall(uint32_t *T, int64_t ldt, int D, int rw, 
 // padded to 4 words) and, when tc and room allow, the tensor-core operands of a D^3 product
 size_t bool_squaring_workspace(int64_t D, int64_t rw);
 sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, void *ws, size_t ws_bytes, bool tc,
-                                       int *status, int spin_limit, cudaStream_t s);
+                                       int *status, int spin_limit, cudaStream_t s, int grid_sms = 0);
 // Blocked Warshall with kBoolWideBlock-bit blocks and phase 3 on the tensor cores; ws as
 // for launch_bool_mul_tc, at least bool_closure_wide_workspace(D) bytes
 constexpr int kBoolWideBlock = 2048;
