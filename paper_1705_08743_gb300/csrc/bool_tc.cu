@@ -47,6 +47,7 @@ struct BoolTcArgs {
     int *status;          // nonzero after a bounded wait gave up (may be null)
     uint32_t wait_limit;  // tries per wait before giving up (the context's spin limit)
     int hole_r0, hole_rn, hole_w0, hole_wn;   // tiles inside this block of C are skipped
+    int band_r0, band_rn, band_w0, band_wn;   // and tiles inside this row band or word band
     const int *run_if;    // device flag: the product is skipped (C untouched) when it reads 0 (may be null)
 };
 
@@ -153,9 +154,14 @@ __device__ __forceinline__ bool tc_tile(const BoolTcArgs &p, int t, int &row0, i
     const int r = t - g * per_group;
     row0 = (first_m + r % gm) * tc::BM;
     ncol0 = (r / gm) * tc::BN;
-    if (p.hole_rn > 0) {
+    if (p.hole_rn > 0 || p.band_rn > 0 || p.band_wn > 0) {
         const int w0 = ncol0 >> 5, r1 = min(row0 + tc::BM, p.R), w1 = min(w0 + tc::BN / 32, p.ncw);
-        if (row0 >= p.hole_r0 && r1 <= p.hole_r0 + p.hole_rn && w0 >= p.hole_w0 && w1 <= p.hole_w0 + p.hole_wn)
+        if (p.hole_rn > 0 && row0 >= p.hole_r0 && r1 <= p.hole_r0 + p.hole_rn && w0 >= p.hole_w0 &&
+            w1 <= p.hole_w0 + p.hole_wn)
+            return false;
+        if (p.band_rn > 0 && row0 >= p.band_r0 && r1 <= p.band_r0 + p.band_rn)
+            return false;
+        if (p.band_wn > 0 && w0 >= p.band_w0 && w1 <= p.band_w0 + p.band_wn)
             return false;
     }
     return true;
@@ -578,6 +584,12 @@ sr_status launch_bool_mul_tc(const BoolArgs &a, void *ws, size_t ws_bytes, int *
         if (!rows_ok || !words_ok || a.hole_r0 < 0 || a.hole_w0 < 0 || a.hole_wn <= 0)
             return fail(SR_EINVAL, "bool_mul (tensor path): the untouched block must lie on the 128 x 256 tile grid");
     }
+    if (a.band_rn < 0 || a.band_wn < 0 ||
+        (a.band_rn > 0 && (a.band_r0 < 0 || a.band_r0 % tc::BM != 0 ||
+                           ((a.band_r0 + a.band_rn) % tc::BM != 0 && a.band_r0 + a.band_rn < a.R))) ||
+        (a.band_wn > 0 && (a.band_w0 < 0 || a.band_w0 % (tc::BN / 32) != 0 ||
+                           ((a.band_w0 + a.band_wn) % (tc::BN / 32) != 0 && a.band_w0 + a.band_wn < a.ncw))))
+        return fail(SR_EINVAL, "bool_mul (tensor path): the untouched bands must lie on the 128 x 256 tile grid");
     uint8_t *Ae = static_cast<uint8_t *>(ws);
     uint8_t *Be = tc_operand_b(Ae, a.R, Kp);
     const int sms = device_sm_count();
@@ -646,6 +658,7 @@ sr_status launch_bool_mul_tc_expanded(const BoolArgs &a, uint8_t *Ae, uint8_t *B
     p.status = status;
     p.wait_limit = (uint32_t)std::max(0, spin_limit);
     p.hole_r0 = a.hole_r0; p.hole_rn = a.hole_rn; p.hole_w0 = a.hole_w0; p.hole_wn = a.hole_wn;
+    p.band_r0 = a.band_r0; p.band_rn = a.band_rn; p.band_w0 = a.band_w0; p.band_wn = a.band_wn;
     p.run_if = run_if;
     p.tiles_n = (a.ncw + tc::BN / 32 - 1) / (tc::BN / 32);
     p.tiles_m = (a.R + tc::BM - 1) / tc::BM;

@@ -710,10 +710,11 @@ sr_status launch_bool_closure_squaring(uint32_t *T, int64_t ldt, int D, int rw, 
 //            panel over every row i, side by side on the tensor cores (j = k and i = k
 //            change nothing: T_kk ⊗ T_kk <= T_kk once T_kk is closed; the two products
 //            overlap only in T_kk, which neither changes);
-//   phase 3: T := T ⊕ T_col k ⊗ T_row k over the whole matrix except the diagonal block
-//            kb+1 (again the panels themselves do not change), while a side stream gives
-//            block (kb+1, kb+1) its update from kb and closes it by repeated squaring on
-//            the tensor cores (phase 1 of kb+1: log2 W + 1 products of W^3; the 128-bit
+//   phase 3: T := T ⊕ T_col k ⊗ T_row k over the whole matrix except block row and
+//            column kb (the panels, which it would not change; skipping them saves a
+//            quarter of its tiles at D = 16384) and the diagonal block kb+1, while a side
+//            stream gives block (kb+1, kb+1) its update from kb and closes it by repeated
+//            squaring on the tensor cores (phase 1 of kb+1: log2 W + 1 products of W^3; the 128-bit
 //            Warshall schedule's 16 dependent pivot blocks took 0.74 ms beside phase 3,
 //            longer than phase 3 itself).
 // The operands of every tensor-core product are expanded into the workspace before its
@@ -796,6 +797,9 @@ sr_status launch_bool_closure_wide(uint32_t *T, int64_t ldt, int D, int rw, void
             SR_CUDA_CHECK(cudaEventRecord(diag_done[kb + 1], sp));
         }
         BoolArgs p3 = bool_args(T + kw, T + (int64_t)k0 * ldt, T, ldt, D, bw, D, rw);
+        // block row and column kb are the panels, which phase 3 would leave as they are
+        p3.band_r0 = k0; p3.band_rn = bw;
+        p3.band_w0 = kw; p3.band_wn = wn;
         if (next) {
             p3.hole_r0 = k1; p3.hole_rn = width(kb + 1);
             p3.hole_w0 = kw1; p3.hole_wn = words_of(kb + 1);

@@ -115,6 +115,10 @@ struct BoolArgs {
     // words [hole_w0, hole_w0 + hole_wn) (hole_rn = 0: none); its edges must fall on the
     // 128-row x 8-word tile grid or at the end of C
     int hole_r0 = 0, hole_rn = 0, hole_w0 = 0, hole_wn = 0;
+    // tensor-core path only: a band of rows [band_r0, band_r0 + band_rn) across all words and
+    // a band of words [band_w0, band_w0 + band_wn) down all rows, also left untouched (0: none);
+    // edges on the same grid as the hole's
+    int band_r0 = 0, band_rn = 0, band_w0 = 0, band_wn = 0;
 };
 // shape: 0 = 128 rows x 64 words per CTA, 1 = 128 x 4 (narrow panels), 2 = 32 x 16 (short panels)
 sr_status launch_bool_mul(const BoolArgs &a, bool vec, cudaStream_t s, int shape = 0);
